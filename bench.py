@@ -1,0 +1,481 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Gauss-Jordan inversion library.
+
+Default workload: one 8192 x 8192 FP64 matrix, N(0,1) entries + 0.1 n on the diagonal,
+partial pivoting, blocked path (cluster panel + rank-b update).  A step is one whole
+inversion through the C ABI (copy-in, every panel and update, un-permutation,
+determinant) with the input already resident in device memory.  The metric is inverse
+GFLOP/s counted as 2 n^3 per inverse.
+
+Other workloads (``--workload``): ``inv128`` (one 128 x 128 N(0,1) matrix, full pivoting)
+and ``batch200k`` (200,000 matrices, orders uniform in 4..64, diagonally dominant,
+partial pivoting, one persistent launch replayed as a CUDA graph; metric matrices/s).
+
+``--impl reference`` times the CPU oracle (plain FP64 C, the test reference) on the host
+cores on a bounded sample of the same workload and prints the same JSON line.
+
+Multi-GPU (torchrun): each rank inverts its own matrices (independent problems, no
+data-path collective); value = work of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1401_7962_gb300 import workloads as wl  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Nominal GB300 FP64 rate: 152 SMs x 2 FP64 FMA lanes per clock x 2 FLOP x ~2.06 GHz.
+FP64_NOMINAL_GFLOPS = 1250.0
+
+WORKLOADS = {
+    "inv8192": dict(n=8192, shift=0.1, pivot=1, seed=wl.SEED_BASE + 2,
+                    name="gj-inverse-8192-fp64-partial-blocked"),
+    "inv128": dict(n=128, shift=0.0, pivot=2, seed=wl.SEED_BASE + 1, name="gj-inverse-128-fp64-full-cta"),
+    "batch200k": dict(count=200_000, seed=wl.SEED_BASE + 3, pivot=1,
+                      name="gj-batched-200k-n4to64-fp64-partial"),
+}
+
+
+# ----------------------------------------------------------------- distributed helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def shard_lpt(sizes: np.ndarray, world: int) -> list[np.ndarray]:
+    """Split matrix indices over ranks by n^3, largest first, each to the least-loaded rank."""
+    order = np.argsort(-(sizes.astype(np.float64) ** 3), kind="stable")
+    load = np.zeros(world)
+    parts = [[] for _ in range(world)]
+    for m in order:
+        r = int(np.argmin(load))
+        parts[r].append(int(m))
+        load[r] += float(sizes[m]) ** 3
+    return [np.array(sorted(p), dtype=np.int64) for p in parts]
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- peaks
+
+def measured_peaks() -> dict:
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline_fp64(achieved_gflops: float, traffic) -> dict:
+    # FP64 FMA is plain ALU work on GB300 (DMMA measures no faster than DFMA), so the
+    # peak is the FP64 unit rate, not a tensor rate.
+    return {"bound": "alu", "achieved": round(achieved_gflops / 1000.0, 4), "peak": FP64_NOMINAL_GFLOPS / 1000.0,
+            "unit": "TFLOP/s", "frac": round(achieved_gflops / FP64_NOMINAL_GFLOPS, 4), "traffic": traffic,
+            "peak_source": "nominal FP64 unit rate (152 SMs x 4 FLOP/clk x 2.06 GHz); DFMA probe measured 1.197"}
+
+
+# ----------------------------------------------------------------- CPU oracle legs
+
+def cpu_oracle_sample(workload: str, repeat: int = 1) -> dict:
+    """The oracle as it stands on a bounded sample of the workload; returns value/unit/cores/sample."""
+    import oracle
+    W = WORKLOADS[workload]
+    if workload == "batch200k":
+        sizes, packed, offsets = wl.diag_dominant_batch(W["count"], W["seed"])
+        take = 40_000
+        sizes, offsets = sizes[:take], offsets[:take]
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        for _ in range(repeat):
+            oracle.invert_many(sizes, packed, offsets, W["pivot"], threads=cores)
+        dt = (time.perf_counter() - t0) / repeat
+        return {"value": take / dt, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+                "sample": f"first {take} of the 200000 matrices, oracle over {cores} threads",
+                "gflops": float((2.0 * sizes.astype(np.float64) ** 3).sum() / dt / 1e9)}
+    n = 2048 if workload == "inv8192" else W["n"]
+    A = wl.gaussian(n, W["seed"], shift=W["shift"] * n)
+    reps = repeat if workload == "inv8192" else max(repeat, 50)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.invert(A, W["pivot"])
+    dt = (time.perf_counter() - t0) / reps
+    samp = (f"one {n}x{n} matrix of the same recipe (N(0,1)+0.1nI), partial pivoting, 1 thread"
+            if workload == "inv8192" else f"the {n}x{n} matrix, full pivoting, 1 thread, mean of {reps}")
+    return {"value": 2.0 * n ** 3 / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": samp}
+
+
+def run_reference(args) -> None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    W = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args.workload)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(args.workload))
+    wall = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": metric_name(args.workload), "value": v, "unit": cb["unit"],
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"], "sample": cb["sample"]},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": v, "unit": cb["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def metric_name(workload: str) -> str:
+    return "inverse GFLOP/s (2n^3)" if workload != "batch200k" else "batched matrices/s"
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_gpu(args) -> None:
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1401_7962_gb300 import _build
+    _build.build()
+    import paper_1401_7962_gb300 as gj
+    import ctypes
+    L = gj.lib()
+    W = WORKLOADS[args.workload]
+    stream = torch.cuda.Stream(device=dev)
+    Entry = _profile_struct()[0]
+    prof_entries = (Entry * 16)()
+    per_launch_flops = 0.0
+
+    extra = {}
+    if args.workload == "batch200k":
+        sizes, packed, offsets = wl.diag_dominant_batch(W["count"], W["seed"] + rank)
+        count = len(sizes)
+        dA = torch.from_numpy(packed).to(dev)
+        dX = torch.empty_like(dA)
+        ap = torch.from_numpy(dA.data_ptr() + 8 * offsets).to(dev)
+        xp = torch.from_numpy(dX.data_ptr() + 8 * offsets).to(dev)
+        st = torch.zeros(count, dtype=torch.int32, device=dev)
+        sg = torch.zeros(count, dtype=torch.int8, device=dev)
+        lg = torch.zeros(count, dtype=torch.float64, device=dev)
+        plan = gj.BatchedPlan(sizes, W["pivot"])
+        flops_step = float((2.0 * sizes.astype(np.float64) ** 3).sum())
+        bytes_step = float(16.0 * (sizes.astype(np.float64) ** 2).sum())
+        units_step = count
+
+        def step():
+            plan.execute(ap, xp, st, sg, lg, stream=stream, use_graph=True)
+
+        dominant = "cta_batched"
+        per_launch_flops = flops_step
+        h2d = packed.nbytes + 8 * count * 2 + 4 * count
+        d2h = packed.nbytes + count * (4 + 1 + 8)
+    else:
+        n = W["n"]
+        A = wl.gaussian(n, W["seed"] + rank, shift=W["shift"] * n)
+        dA = torch.from_numpy(A).to(dev)
+        dX = torch.empty_like(dA)
+        flops_step = 2.0 * n ** 3
+        units_step = 1
+        sgn, lg2 = ctypes.c_int(0), ctypes.c_double(0.0)
+        opts = gj._Opts()
+        opts.stream = stream.cuda_stream
+        opts.update = {"auto": 0, "dfma": 1, "ozaki": 2}[args.update]
+
+        def step():
+            stc = L.gj_invert_ex(ctypes.byref(opts), n, dA.data_ptr(), n, dX.data_ptr(), W["pivot"],
+                                 ctypes.byref(sgn), ctypes.byref(lg2))
+            if stc != 0:
+                raise RuntimeError(f"gj_invert_ex failed: {gj.status_string(stc)} {gj.last_error()}")
+
+        dominant = "update_dfma" if args.workload == "inv8192" else "cta_single"
+        h2d = d2h = n * n * 8
+
+    # ---- warm-up
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    # ---- timed region
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    L.gj_profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+    e1.synchronize()
+    launches = ctypes.c_int64(0)
+    cnt = L.gj_profile_end(prof_entries, 16, ctypes.byref(launches))
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    prof = {}
+    for i in range(cnt):
+        e = prof_entries[i]
+        prof[e.kernel.decode()] = {"launches": e.launches, "total_ms": e.total_ms, "flops": e.flops, "bytes": e.bytes}
+
+    total_units = units_step * args.steps * world
+    total_flops = flops_step * args.steps * world
+    if args.workload == "batch200k":
+        value = total_units / (ms_max / 1000.0)
+        unit = "matrices/s"
+        extra["gflops"] = total_flops / (ms_max / 1000.0) / 1e9
+    else:
+        value = total_flops / (ms_max / 1000.0) / 1e9
+        unit = "GFLOP/s"
+
+    roof = None
+    if dominant in prof and prof[dominant]["launches"]:
+        d = prof[dominant]
+        avg_ms = d["total_ms"] / d["launches"]
+        fl = d["flops"] / d["launches"] if d["flops"] else per_launch_flops
+        achieved_gflops = fl / (avg_ms / 1000.0) / 1e9
+        roof = roofline_fp64(achieved_gflops, args.traffic)
+        roof["kernel"] = dominant
+        roof["avg_launch_ms"] = round(avg_ms, 6)
+        roof["share_of_step"] = round(d["total_ms"] / ms, 4)
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if rank == 0 or world > 1:
+        e2e = run_e2e(args, gj, L, W, stream, dev, h2d, d2h, units_step, flops_step, rank)
+        if world > 1:
+            e2e["value"] = e2e["value"]  # per-rank; aggregate below
+            tmax = max_over_ranks(e2e.pop("_seconds"), world)
+            e2e["value"] = (total_units if args.workload == "batch200k" else total_flops / 1e9) / tmax
+        else:
+            e2e.pop("_seconds", None)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample(args.workload)
+        cpu.pop("gflops", None)
+
+    if rank == 0:
+        cfg = {"workload": W["name"], "pivot": ["none", "partial", "full"][W["pivot"]],
+               "l2": "inputs larger than L2 (no flush)" if args.workload != "inv128" else
+               "128 KiB matrix is L2-resident; latency-bound single CTA (no flush)",
+               "profile": prof}
+        if args.workload == "inv8192":
+            cfg.update({"n": W["n"], "update": args.update, "input": "N(0,1) + 0.1 n I, seed 1403"})
+        elif args.workload == "inv128":
+            cfg.update({"n": W["n"], "input": "N(0,1), seed 1402"})
+        else:
+            cfg.update({"count": W["count"], "orders": "U{4..64}", "input": "U[-1,1], diag 1+sum|row|, seed 1404",
+                        "launch": "plan + CUDA graph"})
+        cfg.update(extra)
+        line = {"metric": metric_name(args.workload), "value": value, "unit": unit, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": int(launches.value)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _profile_struct():
+    import ctypes
+
+    class Entry(ctypes.Structure):
+        _fields_ = [("kernel", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                    ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+    return (Entry,)
+
+
+def run_e2e(args, gj, L, W, stream, dev, h2d, d2h, units_step, flops_step, rank) -> dict:
+    """The same metric through the public API with pinned host buffers: every step copies
+    the inputs host -> device and the results device -> host inside the timed region."""
+    import ctypes
+    import torch
+    steps = max(1, min(args.steps, 3)) if args.workload == "inv8192" else args.steps
+    if args.workload == "batch200k":
+        sizes, packed, offsets = wl.diag_dominant_batch(W["count"], W["seed"] + rank)
+        count = len(sizes)
+        hA = torch.from_numpy(packed).pin_memory()
+        hX = torch.empty_like(hA).pin_memory()
+        h_off = torch.from_numpy(offsets).pin_memory()
+        h_st = torch.empty(count, dtype=torch.int32).pin_memory()
+        h_sg = torch.empty(count, dtype=torch.int8).pin_memory()
+        h_lg = torch.empty(count, dtype=torch.float64).pin_memory()
+        dA = torch.empty(hA.shape, dtype=torch.float64, device=dev)
+        dX = torch.empty_like(dA)
+        d_off = torch.empty(count, dtype=torch.int64, device=dev)
+        st = torch.empty(count, dtype=torch.int32, device=dev)
+        sg = torch.empty(count, dtype=torch.int8, device=dev)
+        lg = torch.empty(count, dtype=torch.float64, device=dev)
+        n_dev = torch.from_numpy(sizes).to(dev)
+
+        def one():
+            with torch.cuda.stream(stream):
+                dA.copy_(hA, non_blocking=True)
+                d_off.copy_(h_off, non_blocking=True)
+                ap = d_off * 8 + dA.data_ptr()
+                xp = d_off * 8 + dX.data_ptr()
+                gj.invert_batched(n_dev, ap, xp, st, sg, lg, pivot_mode=W["pivot"], nmax=64, stream=stream)
+                hX.copy_(dX, non_blocking=True)
+                h_st.copy_(st, non_blocking=True)
+                h_sg.copy_(sg, non_blocking=True)
+                h_lg.copy_(lg, non_blocking=True)
+            stream.synchronize()
+    else:
+        n = W["n"]
+        A = wl.gaussian(n, W["seed"] + rank, shift=W["shift"] * n)
+        hA = torch.from_numpy(A).pin_memory()
+        hX = torch.empty_like(hA).pin_memory()
+        sgn, lg2 = ctypes.c_int(0), ctypes.c_double(0.0)
+        opts = gj._Opts()
+        opts.stream = stream.cuda_stream
+
+        def one():
+            stc = L.gj_invert_ex(ctypes.byref(opts), n, hA.data_ptr(), n, hX.data_ptr(), W["pivot"],
+                                 ctypes.byref(sgn), ctypes.byref(lg2))
+            if stc != 0:
+                raise RuntimeError(gj.status_string(stc))
+
+    one()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    if args.workload == "batch200k":
+        val = units_step * steps / dt
+        unit = "matrices/s"
+    else:
+        val = flops_step * steps / dt / 1e9
+        unit = "GFLOP/s"
+    return {"value": val, "unit": unit, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps, "_seconds": dt / steps}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gj", "reference"], default="gj")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="inv8192")
+    ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gj":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

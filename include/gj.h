@@ -1,0 +1,188 @@
+/*
+ * gj.h -- C ABI of the GB300 (sm_103a) Gauss-Jordan inversion library.
+ *
+ * The method is the Gauss-Jordan inversion of arXiv:1401.7962, Section 2: the pair
+ * [A | D], initialised to [A | I] (eqs. 1-2), is reduced in n steps to [I | A^-1]
+ * (eqs. 11-12).  Step k divides the pivot row by the pivot (eq. 14) and subtracts
+ * multiples of it from every other row (eq. 15); the pivot is the entry of largest
+ * magnitude among the candidates (observations 2-3) and the interchanges are undone
+ * at the end; det A is the product of the pivots (eq. 13) with one sign change per
+ * interchange.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major.  Element (i, j) of A is A[i + j * lda].  The inverse
+ *     is written with leading dimension n.
+ *   - Floating point is IEEE binary64 unless an entry point says otherwise.
+ *   - Pointers the caller passes are owned by the caller.  The library allocates only
+ *     internal workspace (stream-ordered, freed before the call returns or, for
+ *     stream-ordered calls, in stream order) and never frees caller memory.
+ *   - Where a pointer is documented "host or device" the library inspects it
+ *     (cudaPointerGetAttributes) and stages host buffers through device memory.
+ *   - Steps are numbered from 0 (the paper numbers them from 1).  Pivot positions
+ *     returned by the library are 0-based positions at the time of the step, i.e.
+ *     the index of the row (column) interchanged with row (column) k at step k, as
+ *     in the paper's program, which records the row it swaps with row k.
+ *   - Errors are reported by return value.  Argument errors are detected before any
+ *     launch.  A CUDA error is returned as GJ_ERR_CUDA; gj_last_error() then gives
+ *     the CUDA error text.  There is no CPU fallback: every step of the inversion
+ *     runs in the library's CUDA kernels.
+ */
+#ifndef GJ_H
+#define GJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Result codes. */
+typedef enum gj_status {
+  GJ_OK = 0,
+  GJ_SINGULAR = 1,       /* every candidate of some step was 0 or <= tau (obs. 2: "all
+                            possibilities fail"); det_sign = 0, det_log2 = -inf */
+  GJ_ZERO_PIVOT = 2,     /* pivot mode NONE met a pivot with |a_kk| <= tau; obs. 2 notes
+                            this does not imply that A is singular */
+  GJ_NONFINITE = 3,      /* a candidate of some step was NaN or infinite */
+  GJ_NOT_CONVERGED = 4,  /* iterative refinement did not reach the tolerance */
+  GJ_ERR_ARG = -1,       /* invalid argument; nothing was launched */
+  GJ_ERR_CUDA = -2,      /* a CUDA call failed; see gj_last_error() */
+  GJ_ERR_NOMEM = -3,     /* workspace allocation failed */
+  GJ_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up (grid or cluster barrier) */
+  GJ_ERR_UNSUPPORTED = -5 /* the combination of sizes and options has no kernel */
+} gj_status;
+
+/* Pivot selection (observations 2-3). */
+typedef enum gj_pivot {
+  GJ_PIVOT_NONE = 0,     /* pivot a_kk as it stands (eqs. 3-15 without interchanges) */
+  GJ_PIVOT_PARTIAL = 1,  /* largest |a_ik| over the rows not yet used; ties to the
+                            smallest row position */
+  GJ_PIVOT_FULL = 2      /* largest |a_ij| over unused rows and columns; ties to the
+                            smallest column position, then the smallest row position */
+} gj_pivot;
+
+/* Options for gj_invert_ex.  Zero-initialise and set what you need. */
+typedef struct gj_opts {
+  void* stream;          /* cudaStream_t to run on; NULL = the legacy default stream */
+  double tau;            /* zero threshold of obs. 2: a step fails when the largest
+                            candidate magnitude is <= tau.  Must be >= 0.  Default 0 */
+  int32_t panel;         /* panel width b of the blocked path (16, 32 or 64); 0 = library
+                            choice.  Ignored by the single-CTA path */
+  int32_t path;          /* 0 = automatic; 1 = single-CTA shared-memory kernel (n <= 128);
+                            2 = blocked panel + rank-b update (partial / none pivoting);
+                            3 = unblocked multi-CTA (any pivoting, any n) */
+  int32_t update;        /* blocked path rank-b update engine: 0 = automatic, 1 = FP64 DFMA,
+                            2 = FP64 emulated on BF16 tcgen05 tensor cores (split operands,
+                            exact FP32 partial sums, FP64 recombination) */
+  int32_t reserved0;
+  int32_t* piv_rows;     /* optional out [n], host or device: row position interchanged
+                            with position k at step k */
+  int32_t* piv_cols;     /* optional out [n], host or device: same for columns */
+  double* pivots;        /* optional out [n], host or device: pivot value of step k (the
+                            eq. 13 factors) */
+  int64_t* fail_step;    /* optional out, host: failing step, -1 on success */
+} gj_opts;
+
+/*
+ * gj_invert -- invert one n x n matrix (eqs. 1-15, obs. 2-3).
+ *   n          order, n >= 0.  n == 0 returns GJ_OK with det_sign = 1, det_log2 = 0.
+ *   A          [lda * n] input, host or device.  Not modified unless Ainv == A.
+ *   lda        leading dimension of A, lda >= max(1, n).
+ *   Ainv       [n * n] output, host or device, leading dimension n.  Ainv == A is allowed
+ *              when lda == n (in-place inversion).  Contents are unspecified when the
+ *              status is not GJ_OK.
+ *   pivot_mode a gj_pivot value.
+ *   det_sign   out (host, may be NULL): sign of det A, one of -1, +1; 0 on failure.
+ *   det_log2   out (host, may be NULL): log2 |det A|; -inf on failure.
+ * Synchronous: returns after the result is in Ainv.  Runs on the legacy default stream.
+ */
+gj_status gj_invert(int64_t n, const double* A, int64_t lda, double* Ainv, int pivot_mode, int* det_sign,
+                    double* det_log2);
+
+/* gj_invert_ex -- gj_invert with options (stream, tau, path, pivot record).  opts may be
+ * NULL (same as gj_invert).  Synchronous with respect to the host: it waits on
+ * opts->stream before returning, because det_sign / det_log2 are host values. */
+gj_status gj_invert_ex(const gj_opts* opts, int64_t n, const double* A, int64_t lda, double* Ainv,
+                       int pivot_mode, int* det_sign, double* det_log2);
+
+/*
+ * gj_invert_batched -- invert `count` independent matrices of uneven orders in one
+ * persistent launch (one CTA per matrix; work items taken largest order first).
+ *   count      number of matrices, >= 0.
+ *   nmax       host: upper bound of the orders (sizes the launch); 0 means 128.  Must
+ *              be <= 128 (GJ_ERR_UNSUPPORTED otherwise).
+ *   n          [count] device: orders, 0 <= n[m] <= nmax (a matrix outside that range
+ *              gets status[m] = GJ_ERR_ARG and is not touched).
+ *   A          [count] device array of device pointers: matrix m, column-major, ld n[m].
+ *   Ainv       [count] device array of device pointers: output m, column-major, ld n[m].
+ *              Ainv[m] == A[m] is allowed.
+ *   pivot_mode a gj_pivot value, shared by all matrices.
+ *   status     [count] device out: per-matrix gj_status.
+ *   det_sign   [count] device out (may be NULL): -1, +1, or 0 on failure.
+ *   det_log2   [count] device out (may be NULL): log2 |det|, -inf on failure.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * Stream-ordered: returns after enqueueing; no host synchronisation.  Needs a device
+ * workspace of (count + 130) int32 taken from the stream-ordered allocator.
+ */
+gj_status gj_invert_batched(int64_t count, int32_t nmax, const int32_t* n, const double* const* A,
+                            double* const* Ainv, int pivot_mode, int32_t* status, int8_t* det_sign,
+                            double* det_log2, void* stream);
+
+/* A batched plan fixes the orders (host copy given at creation), precomputes the
+ * largest-first work order and launch shape, and can be replayed as a CUDA graph. */
+typedef struct gj_plan gj_plan;
+
+/*
+ * gj_batched_plan_create -- plan a batch.
+ *   plan     out: the new plan.
+ *   count    number of matrices.
+ *   n_host   [count] host: orders (0 <= n <= 128).
+ *   pivot_mode  gj_pivot value.
+ * The plan owns device copies of the orders and the work order.
+ */
+gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n_host, int pivot_mode);
+
+/*
+ * gj_batched_plan_execute -- run a planned batch on `stream`.  Argument meaning as in
+ * gj_invert_batched (device arrays).  With use_graph != 0 the launch sequence is
+ * captured once into a CUDA graph for these pointer arrays and replayed afterwards
+ * (re-captured if the pointers or stream change).
+ */
+gj_status gj_batched_plan_execute(gj_plan* plan, const double* const* A, double* const* Ainv, int32_t* status,
+                                  int8_t* det_sign, double* det_log2, void* stream, int use_graph);
+
+/* gj_batched_plan_destroy -- free a plan (NULL is allowed). */
+void gj_batched_plan_destroy(gj_plan* plan);
+
+/* Kernel timing for benchmarks (no counterpart in the paper).  Between
+ * gj_profile_begin() and gj_profile_end() the library records a CUDA event pair on the
+ * launching stream around each launch of its dominant kernels and counts every kernel
+ * it launches.  gj_profile_end() waits for those events and fills up to max_entries
+ * aggregates (one per kernel name, `kernel` points to static text); it returns the
+ * number of aggregates and stores the total number of kernel launches in *launches.
+ * Process-wide state; not meant to be used from several threads at once. */
+typedef struct gj_profile_entry {
+  const char* kernel;
+  int64_t launches;
+  double total_ms;   /* summed device time of those launches */
+  double flops;      /* summed algorithmic FLOP count declared by the launch site */
+  double bytes;      /* summed algorithmic DRAM bytes declared by the launch site */
+} gj_profile_entry;
+
+gj_status gj_profile_begin(void);
+int gj_profile_end(gj_profile_entry* out, int max_entries, int64_t* launches);
+
+/* gj_status_string -- static text for a status code. */
+const char* gj_status_string(int status);
+
+/* gj_last_error -- text of the last CUDA error seen by this thread ("" if none). */
+const char* gj_last_error(void);
+
+/* gj_version -- library version string. */
+const char* gj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GJ_H */

@@ -1,1 +1,235 @@
-"""GB300-native Gauss-Jordan inversion (arXiv:1401.7962) -- Python binding of the C-ABI library."""
+"""GB300-native Gauss-Jordan inversion (arXiv:1401.7962) -- Python binding of the C-ABI library.
+
+The library (``_lib/libgj.so``, built from ``csrc/*.cu`` for sm_103a) does every step of
+the inversion in its own CUDA kernels; this module only marshals arguments (pointers,
+sizes, strides, streams) into the C entry points declared in ``include/gj.h``.  There
+is no CPU fallback: if the library is not built, every call raises ``RuntimeError``.
+
+Matrices are column-major.  A torch tensor or numpy array ``A`` of shape (n, n) is
+accepted when its column stride is its leading dimension and its row stride is 1
+(``A.t().contiguous().t()`` for torch, ``numpy.asfortranarray`` for numpy).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = ["lib", "invert", "invert_batched", "BatchedPlan", "GJError", "colmajor", "status_string",
+           "PIVOT_NONE", "PIVOT_PARTIAL", "PIVOT_FULL"]
+
+OK, SINGULAR, ZERO_PIVOT, NONFINITE, NOT_CONVERGED = 0, 1, 2, 3, 4
+ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+PIVOT_NONE, PIVOT_PARTIAL, PIVOT_FULL = 0, 1, 2
+PATH_AUTO, PATH_CTA, PATH_BLOCKED, PATH_UNBLOCKED = 0, 1, 2, 3
+UPDATE_AUTO, UPDATE_DFMA, UPDATE_TC_OZAKI = 0, 1, 2
+
+
+class GJError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status}) {last_error()}".rstrip())
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("tau", ctypes.c_double), ("panel", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("update", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("piv_rows", ctypes.c_void_p), ("piv_cols", ctypes.c_void_p), ("pivots", ctypes.c_void_p),
+                ("fail_step", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library; raises RuntimeError when it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built ({path}); run paper_1401_7962_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    P, I64, I32, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int
+    L.gj_invert.restype = I
+    L.gj_invert.argtypes = [I64, P, I64, P, I, P, P]
+    L.gj_invert_ex.restype = I
+    L.gj_invert_ex.argtypes = [ctypes.POINTER(_Opts), I64, P, I64, P, I, P, P]
+    L.gj_invert_batched.restype = I
+    L.gj_invert_batched.argtypes = [I64, I32, P, P, P, I, P, P, P, P]
+    L.gj_batched_plan_create.restype = I
+    L.gj_batched_plan_create.argtypes = [ctypes.POINTER(P), I64, P, I]
+    L.gj_batched_plan_execute.restype = I
+    L.gj_batched_plan_execute.argtypes = [P, P, P, P, P, P, P, I]
+    L.gj_batched_plan_destroy.restype = None
+    L.gj_batched_plan_destroy.argtypes = [P]
+    L.gj_status_string.restype = ctypes.c_char_p
+    L.gj_status_string.argtypes = [I]
+    L.gj_last_error.restype = ctypes.c_char_p
+    L.gj_last_error.argtypes = []
+    L.gj_version.restype = ctypes.c_char_p
+    L.gj_version.argtypes = []
+    _LIB = L
+    return L
+
+
+def status_string(status: int) -> str:
+    return lib().gj_status_string(int(status)).decode()
+
+
+def last_error() -> str:
+    return lib().gj_last_error().decode()
+
+
+# ----------------------------------------------------------------- marshalling helpers
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if _is_torch(x):
+        return int(x.data_ptr())
+    return int(x.ctypes.data)
+
+
+def _colmajor_ld(A) -> tuple[int, int]:
+    """(n, lda) of a square column-major matrix, or ValueError."""
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square 2-D matrix expected")
+    n = int(A.shape[0])
+    if _is_torch(A):
+        if A.dtype.__repr__() != "torch.float64":
+            raise TypeError("float64 matrix expected")
+        s0, s1 = A.stride()
+    else:
+        if str(A.dtype) != "float64":
+            raise TypeError("float64 matrix expected")
+        s0, s1 = (A.strides[0] // 8, A.strides[1] // 8)
+    if n <= 1:
+        return n, max(n, 1)
+    if s0 != 1 or s1 < n:
+        raise ValueError("matrix must be column-major (row stride 1, column stride >= n)")
+    return n, int(s1)
+
+
+def colmajor(A):
+    """Column-major copy of a square torch tensor or numpy array (same device)."""
+    if _is_torch(A):
+        return A.t().contiguous().t()
+    import numpy as np
+    return np.asfortranarray(A)
+
+
+def _empty_like_colmajor(A, n):
+    if _is_torch(A):
+        import torch
+        return torch.empty((n, n), dtype=torch.float64, device=A.device).t().contiguous().t() if n else \
+            torch.empty((0, 0), dtype=torch.float64, device=A.device)
+    import numpy as np
+    return np.empty((n, n), dtype=np.float64, order="F")
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, path: int = PATH_AUTO,
+           panel: int = 0, update: int = UPDATE_AUTO, stream=None, record: bool = False):
+    """Invert one square matrix with ``gj_invert_ex``.
+
+    ``A`` and ``out`` may live on the host or on the device (the library stages host
+    buffers).  Returns a dict: ``X`` (the output array), ``status``, ``det_sign``,
+    ``det_log2`` and, with ``record=True``, ``piv_rows``, ``piv_cols``, ``pivots``
+    (host numpy arrays) and ``fail_step``.
+    """
+    import numpy as np
+    L = lib()
+    n, lda = _colmajor_ld(A)
+    if out is None:
+        out = _empty_like_colmajor(A, n)
+    else:
+        no, ldo = _colmajor_ld(out)
+        if no != n or (n > 1 and ldo != n):
+            raise ValueError("out must be n x n column-major with leading dimension n")
+    o = _Opts()
+    o.stream = _stream_handle(stream)
+    o.tau = float(tau)
+    o.panel = int(panel)
+    o.path = int(path)
+    o.update = int(update)
+    rec = {}
+    fs = ctypes.c_int64(-1)
+    if record:
+        rec["piv_rows"] = np.full(max(n, 1), -1, dtype=np.int32)
+        rec["piv_cols"] = np.full(max(n, 1), -1, dtype=np.int32)
+        rec["pivots"] = np.zeros(max(n, 1), dtype=np.float64)
+        o.piv_rows = rec["piv_rows"].ctypes.data
+        o.piv_cols = rec["piv_cols"].ctypes.data
+        o.pivots = rec["pivots"].ctypes.data
+    o.fail_step = ctypes.addressof(fs)
+    sgn = ctypes.c_int(0)
+    lg = ctypes.c_double(0.0)
+    st = L.gj_invert_ex(ctypes.byref(o), n, _ptr(A), lda, _ptr(out), int(pivot_mode), ctypes.addressof(sgn),
+                        ctypes.addressof(lg))
+    if st < 0:
+        raise GJError(st, "gj_invert_ex")
+    res = {"X": out, "status": st, "det_sign": sgn.value, "det_log2": lg.value, "fail_step": fs.value}
+    if record:
+        for k in ("piv_rows", "piv_cols", "pivots"):
+            res[k] = rec[k][:n].copy()
+    return res
+
+
+def invert_batched(n_dev, A_ptrs, X_ptrs, status, det_sign=None, det_log2=None, *, pivot_mode: int = PIVOT_PARTIAL,
+                   nmax: int = 0, stream=None) -> None:
+    """Stream-ordered batched inversion (``gj_invert_batched``); all arrays are device tensors.
+
+    ``n_dev`` int32 [count]; ``A_ptrs`` / ``X_ptrs`` int64 [count] device pointers;
+    ``status`` int32 [count]; ``det_sign`` int8 [count]; ``det_log2`` float64 [count].
+    """
+    L = lib()
+    count = int(n_dev.shape[0])
+    st = L.gj_invert_batched(count, int(nmax), _ptr(n_dev), _ptr(A_ptrs), _ptr(X_ptrs), int(pivot_mode),
+                             _ptr(status), _ptr(det_sign), _ptr(det_log2), _stream_handle(stream))
+    if st != OK:
+        raise GJError(st, "gj_invert_batched")
+
+
+class BatchedPlan:
+    """A planned batch (``gj_batched_plan_*``): fixed orders, largest-first order, graph replay."""
+
+    def __init__(self, n_host, pivot_mode: int = PIVOT_PARTIAL):
+        import numpy as np
+        L = lib()
+        self._n = np.ascontiguousarray(n_host, dtype=np.int32)
+        self.count = int(self._n.shape[0])
+        self._plan = ctypes.c_void_p()
+        st = L.gj_batched_plan_create(ctypes.byref(self._plan), self.count, self._n.ctypes.data, int(pivot_mode))
+        if st != OK:
+            raise GJError(st, "gj_batched_plan_create")
+
+    def execute(self, A_ptrs, X_ptrs, status, det_sign=None, det_log2=None, *, stream=None,
+                use_graph: bool = True) -> None:
+        st = lib().gj_batched_plan_execute(self._plan, _ptr(A_ptrs), _ptr(X_ptrs), _ptr(status), _ptr(det_sign),
+                                           _ptr(det_log2), _stream_handle(stream), int(bool(use_graph)))
+        if st != OK:
+            raise GJError(st, "gj_batched_plan_execute")
+
+    def close(self) -> None:
+        if getattr(self, "_plan", None) is not None and self._plan.value:
+            lib().gj_batched_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,368 @@
+// gj_api.cu -- the C ABI: argument checks, host/device staging, path selection.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "gj_internal.cuh"
+#include "gj_paths.cuh"
+
+namespace gj {
+
+static thread_local char g_last_error[512] = "";
+
+gj_status cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return GJ_ERR_CUDA;
+}
+
+namespace {
+
+// True when p is memory the device can address directly as global memory.
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered scratch allocations released in stream order when the scope ends.
+class Scratch {
+ public:
+  explicit Scratch(cudaStream_t s) : s_(s) {}
+  ~Scratch() {
+    for (void* p : ptrs_) cudaFreeAsync(p, s_);
+  }
+  template <class T>
+  gj_status alloc(T** out, size_t count) {
+    void* p = nullptr;
+    size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMallocAsync(&p, bytes, s_);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(g_last_error, sizeof(g_last_error), "cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+      return GJ_ERR_NOMEM;
+    }
+    ptrs_.push_back(p);
+    *out = static_cast<T*>(p);
+    return GJ_OK;
+  }
+
+ private:
+  cudaStream_t s_;
+  std::vector<void*> ptrs_;
+};
+
+#define GJ_TRY(expr)                   \
+  do {                                 \
+    gj_status st_ = (expr);            \
+    if (st_ != GJ_OK) return st_;      \
+  } while (0)
+
+struct ResultBlock {
+  int32_t status;
+  int8_t det_sign;
+  int8_t pad[3];
+  double det_log2;
+  int64_t fail_step;
+};
+
+}  // namespace
+
+// Full single-matrix pipeline on device pointers.  Writes status / det / fail step to
+// the device result block `res`.
+static gj_status run_single_device(const gj_opts& o, int64_t n, const double* dA, int64_t lda, double* dX,
+                                   int pivot_mode, int32_t* d_piv_rows, int32_t* d_piv_cols, double* d_pivots,
+                                   ResultBlock* res, cudaStream_t s) {
+  int path = o.path;
+  if (path == 0) {
+    if (n <= kCtaMaxN) path = 1;
+    else if (pivot_mode == GJ_PIVOT_FULL) path = 3;
+    else path = 2;
+  }
+  CtaOut out{};
+  out.status = &res->status;
+  out.det_sign = &res->det_sign;
+  out.det_log2 = &res->det_log2;
+  out.fail_step = &res->fail_step;
+  out.piv_rows = d_piv_rows;
+  out.piv_cols = d_piv_cols;
+  out.pivots = d_pivots;
+  switch (path) {
+    case 1:
+      if (n > kCtaMaxN) return GJ_ERR_UNSUPPORTED;
+      return launch_cta_single((int)n, dA, lda, dX, pivot_mode, o.tau, out, s);
+    case 2:
+      if (pivot_mode == GJ_PIVOT_FULL) return GJ_ERR_UNSUPPORTED;
+      return run_blocked(n, dA, lda, dX, pivot_mode, o.tau, o.panel, o.update, out, s);
+    case 3:
+      return run_unblocked(n, dA, lda, dX, pivot_mode, o.tau, out, s);
+    default:
+      return GJ_ERR_ARG;
+  }
+}
+
+}  // namespace gj
+
+using namespace gj;
+
+extern "C" {
+
+const char* gj_version(void) { return "gj-gb300 0.1 (sm_103a)"; }
+
+const char* gj_last_error(void) { return g_last_error; }
+
+const char* gj_status_string(int status) {
+  switch (status) {
+    case GJ_OK: return "ok";
+    case GJ_SINGULAR: return "singular: every pivot candidate of a step was zero (or <= tau)";
+    case GJ_ZERO_PIVOT: return "zero pivot without pivoting";
+    case GJ_NONFINITE: return "non-finite pivot candidate";
+    case GJ_NOT_CONVERGED: return "refinement did not converge";
+    case GJ_ERR_ARG: return "invalid argument";
+    case GJ_ERR_CUDA: return "CUDA error";
+    case GJ_ERR_NOMEM: return "out of device memory";
+    case GJ_ERR_TIMEOUT: return "device-side wait timed out";
+    case GJ_ERR_UNSUPPORTED: return "unsupported size / option combination";
+    default: return "unknown status";
+  }
+}
+
+gj_status gj_invert_ex(const gj_opts* opts, int64_t n, const double* A, int64_t lda, double* Ainv, int pivot_mode,
+                       int* det_sign, double* det_log2) {
+  gj_opts o{};
+  if (opts) o = *opts;
+  g_last_error[0] = '\0';
+  if (det_sign) *det_sign = 0;
+  if (det_log2) *det_log2 = -INFINITY;
+  if (o.fail_step) *o.fail_step = -1;
+  if (n < 0 || lda < (n > 0 ? n : 1)) return GJ_ERR_ARG;
+  if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
+  if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
+  if (o.path < 0 || o.path > 3 || o.update < 0 || o.update > 2) return GJ_ERR_ARG;
+  if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
+  if (n == 0) {
+    if (det_sign) *det_sign = 1;
+    if (det_log2) *det_log2 = 0.0;
+    return GJ_OK;
+  }
+  if (!A || !Ainv) return GJ_ERR_ARG;
+  if ((const void*)A == (const void*)Ainv && lda != n) return GJ_ERR_ARG;
+  if (n > 2000000000LL / (n > 0 ? n : 1) && n > 46340) return GJ_ERR_UNSUPPORTED;
+
+  cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+  gj_status result;
+  {
+    Scratch scr(s);
+    const bool a_dev = is_device_ptr(A), x_dev = is_device_ptr(Ainv);
+    const double* dA = A;
+    double* dX = Ainv;
+    int64_t dlda = lda;
+    const size_t nn = (size_t)n * (size_t)n;
+    if (!x_dev) GJ_TRY(scr.alloc(&dX, nn));
+    if (!a_dev) {
+      if ((const void*)A == (const void*)Ainv) {
+        dA = dX;
+      } else {
+        double* t;
+        GJ_TRY(scr.alloc(&t, (size_t)lda * (size_t)n));
+        dA = t;
+      }
+      GJ_CUDA(cudaMemcpyAsync((void*)dA, A, sizeof(double) * ((size_t)lda * (size_t)(n - 1) + (size_t)n),
+                              cudaMemcpyHostToDevice, s));
+    }
+    int32_t* d_pr = nullptr;
+    int32_t* d_pc = nullptr;
+    double* d_pv = nullptr;
+    const bool pr_dev = is_device_ptr(o.piv_rows), pc_dev = is_device_ptr(o.piv_cols),
+               pv_dev = is_device_ptr(o.pivots);
+    if (o.piv_rows) {
+      if (pr_dev) d_pr = o.piv_rows;
+      else GJ_TRY(scr.alloc(&d_pr, (size_t)n));
+    }
+    if (o.piv_cols) {
+      if (pc_dev) d_pc = o.piv_cols;
+      else GJ_TRY(scr.alloc(&d_pc, (size_t)n));
+    }
+    if (o.pivots) {
+      if (pv_dev) d_pv = o.pivots;
+      else GJ_TRY(scr.alloc(&d_pv, (size_t)n));
+    }
+    ResultBlock* d_res;
+    GJ_TRY(scr.alloc(&d_res, 1));
+    GJ_CUDA(cudaMemsetAsync(d_res, 0, sizeof(ResultBlock), s));
+
+    GJ_TRY(run_single_device(o, n, dA, dlda, dX, pivot_mode, d_pr, d_pc, d_pv, d_res, s));
+
+    ResultBlock h{};
+    GJ_CUDA(cudaMemcpyAsync(&h, d_res, sizeof(ResultBlock), cudaMemcpyDeviceToHost, s));
+    if (!x_dev) GJ_CUDA(cudaMemcpyAsync(Ainv, dX, sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+    if (o.piv_rows && !pr_dev) GJ_CUDA(cudaMemcpyAsync(o.piv_rows, d_pr, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    if (o.piv_cols && !pc_dev) GJ_CUDA(cudaMemcpyAsync(o.piv_cols, d_pc, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    if (o.pivots && !pv_dev) GJ_CUDA(cudaMemcpyAsync(o.pivots, d_pv, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    GJ_CUDA(cudaStreamSynchronize(s));
+    result = (gj_status)h.status;
+    if (result == GJ_OK) {
+      if (det_sign) *det_sign = h.det_sign;
+      if (det_log2) *det_log2 = h.det_log2;
+    }
+    if (o.fail_step) *o.fail_step = h.fail_step;
+  }
+  GJ_CUDA(cudaStreamSynchronize(s));  // scratch frees are stream-ordered
+  return result;
+}
+
+gj_status gj_invert(int64_t n, const double* A, int64_t lda, double* Ainv, int pivot_mode, int* det_sign,
+                    double* det_log2) {
+  return gj_invert_ex(nullptr, n, A, lda, Ainv, pivot_mode, det_sign, det_log2);
+}
+
+gj_status gj_invert_batched(int64_t count, int32_t nmax, const int32_t* n, const double* const* A,
+                            double* const* Ainv, int pivot_mode, int32_t* status, int8_t* det_sign,
+                            double* det_log2, void* stream) {
+  g_last_error[0] = '\0';
+  if (count < 0 || count > 0x7fffffffLL) return GJ_ERR_ARG;
+  if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
+  if (nmax <= 0) nmax = kCtaMaxN;
+  if (nmax > kCtaMaxN) return GJ_ERR_UNSUPPORTED;
+  if (count == 0) return GJ_OK;
+  if (!n || !A || !Ainv || !status) return GJ_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Scratch scr(s);
+  int32_t* ws;
+  GJ_TRY(scr.alloc(&ws, (size_t)count + kCtaMaxN + 3));
+  int32_t* order = ws;
+  int32_t* hist = ws + count;
+  int32_t* counter = hist + kCtaMaxN + 1;
+  GJ_TRY(launch_order_by_size(count, n, order, hist, counter, s));
+  CtaOut out{};
+  out.status = status;
+  out.det_sign = det_sign;
+  out.det_log2 = det_log2;
+  return launch_cta_batched(count, nmax, n, A, Ainv, order, counter, pivot_mode, 0.0, out, s);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched plans
+
+struct gj_plan {
+  int64_t count = 0;
+  int nmax = 0;
+  int pivot_mode = 1;
+  int32_t* d_n = nullptr;
+  int32_t* d_order = nullptr;
+  int32_t* d_counter = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+static gj_status plan_enqueue(gj_plan* p, const double* const* A, double* const* Ainv, int32_t* status,
+                              int8_t* det_sign, double* det_log2, cudaStream_t s) {
+  GJ_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int32_t), s));
+  CtaOut out{};
+  out.status = status;
+  out.det_sign = det_sign;
+  out.det_log2 = det_log2;
+  return launch_cta_batched(p->count, p->nmax, p->d_n, A, Ainv, p->d_order, p->d_counter, p->pivot_mode, 0.0, out,
+                            s);
+}
+
+extern "C" {
+
+gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n_host, int pivot_mode) {
+  g_last_error[0] = '\0';
+  if (!plan) return GJ_ERR_ARG;
+  *plan = nullptr;
+  if (count < 0 || count > 0x7fffffffLL || (count > 0 && !n_host)) return GJ_ERR_ARG;
+  if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
+  int nmax = 1;
+  for (int64_t m = 0; m < count; ++m) {
+    if (n_host[m] < 0 || n_host[m] > kCtaMaxN) return GJ_ERR_UNSUPPORTED;
+    nmax = std::max(nmax, (int)n_host[m]);
+  }
+  gj_plan* p = new gj_plan();
+  p->count = count;
+  p->nmax = nmax;
+  p->pivot_mode = pivot_mode;
+  // largest order first (longest-processing-time order for the persistent queue)
+  std::vector<int32_t> order((size_t)count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return n_host[a] > n_host[b]; });
+  cudaError_t e = cudaMalloc(&p->d_n, sizeof(int32_t) * (count > 0 ? count : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int32_t) * (count > 0 ? count : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(int32_t));
+  if (e == cudaSuccess && count > 0) e = cudaMemcpy(p->d_n, n_host, sizeof(int32_t) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && count > 0)
+    e = cudaMemcpy(p->d_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    gj_batched_plan_destroy(p);
+    return cuda_fail(e, "gj_batched_plan_create");
+  }
+  *plan = p;
+  return GJ_OK;
+}
+
+gj_status gj_batched_plan_execute(gj_plan* p, const double* const* A, double* const* Ainv, int32_t* status,
+                                  int8_t* det_sign, double* det_log2, void* stream, int use_graph) {
+  g_last_error[0] = '\0';
+  if (!p) return GJ_ERR_ARG;
+  if (p->count == 0) return GJ_OK;
+  if (!A || !Ainv || !status) return GJ_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!use_graph) return plan_enqueue(p, A, Ainv, status, det_sign, det_log2, s);
+  const void* key[6] = {A, Ainv, status, det_sign, det_log2, stream};
+  bool same = p->exec != nullptr;
+  for (int i = 0; i < 6 && same; ++i) same = (key[i] == p->key[i]);
+  if (!same) {
+    if (p->exec) {
+      cudaGraphExecDestroy(p->exec);
+      p->exec = nullptr;
+    }
+    if (p->graph) {
+      cudaGraphDestroy(p->graph);
+      p->graph = nullptr;
+    }
+    cudaStream_t cap;
+    GJ_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    gj_status st = plan_enqueue(p, A, Ainv, status, det_sign, det_log2, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (st != GJ_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    p->graph = g;
+    GJ_CUDA(cudaGraphInstantiate(&p->exec, g, 0));
+    for (int i = 0; i < 6; ++i) p->key[i] = key[i];
+  }
+  GJ_CUDA(cudaGraphLaunch(p->exec, s));
+  return GJ_OK;
+}
+
+void gj_batched_plan_destroy(gj_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->d_n) cudaFree(p->d_n);
+  if (p->d_order) cudaFree(p->d_order);
+  if (p->d_counter) cudaFree(p->d_counter);
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// gj_internal.cuh -- shared declarations of the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gj.h"
+
+namespace gj {
+
+// ----------------------------------------------------------------- status plumbing
+
+// Record a CUDA error in the thread-local last-error text; returns GJ_ERR_CUDA.
+gj_status cuda_fail(cudaError_t e, const char* what);
+
+#define GJ_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return gj::cuda_fail(e_, #call); \
+  } while (0)
+
+// ----------------------------------------------------------------- profiling
+
+bool prof_enabled();
+void prof_count(int launches);
+
+// Records a CUDA event pair around the launches made during its lifetime when
+// profiling is on; `flops` / `bytes` are the algorithmic counts of those launches.
+class ProfScope {
+ public:
+  ProfScope(cudaStream_t s, const char* name, double flops, double bytes);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaStream_t s_;
+  int rec_;
+};
+
+// ----------------------------------------------------------------- pivot keys
+//
+// Candidate magnitudes are compared as the bit patterns of |v|: for non-negative
+// binary64 values the unsigned integer order of the bit patterns is the numeric order,
+// +inf is 0x7ff0000000000000 and every NaN pattern is larger.  The comparison then
+// runs on the integer pipe instead of the (narrow) FP64 pipe.  Ties are broken by a
+// 32-bit position key: the smaller key wins.
+
+constexpr uint64_t kAbsMask = 0x7fffffffffffffffull;
+constexpr uint64_t kInfBits = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ uint64_t abs_bits(double v) {
+  return static_cast<uint64_t>(__double_as_longlong(v)) & kAbsMask;
+}
+
+__device__ __forceinline__ bool key_better(uint64_t a, int ka, uint64_t b, int kb) {
+  return a > b || (a == b && ka < kb);
+}
+
+__device__ __forceinline__ void warp_argmax(uint64_t& v, int& key) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    uint64_t ov = __shfl_xor_sync(0xffffffffu, v, off);
+    int ok = __shfl_xor_sync(0xffffffffu, key, off);
+    if (key_better(ov, ok, v, key)) {
+      v = ov;
+      key = ok;
+    }
+  }
+}
+
+constexpr int kNoKey = 0x7fffffff;
+
+// ----------------------------------------------------------------- launchers
+
+// Per-matrix outputs of the shared-memory kernel.  Any pointer may be null.
+struct CtaOut {
+  int32_t* status;     // [count] gj_status
+  int8_t* det_sign;    // [count]
+  double* det_log2;    // [count]
+  int32_t* piv_rows;   // [n] (single-matrix launches only)
+  int32_t* piv_cols;   // [n]
+  double* pivots;      // [n]
+  int64_t* fail_step;  // [count]
+};
+
+// Largest order handled by one CTA in shared memory.
+constexpr int kCtaMaxN = 128;
+
+// Shared memory needed by the single-CTA kernel for orders up to nmax.
+size_t cta_smem_bytes(int nmax);
+
+// One matrix, one CTA.  A (ld lda) -> X (ld n); X may equal A when lda == n.
+gj_status launch_cta_single(int n, const double* A, int64_t lda, double* X, int pivot_mode, double tau,
+                            const CtaOut& out, cudaStream_t s);
+
+// Batched persistent launch.  order[q] (q < count) is the matrix processed q-th; the
+// work counter is taken with atomicAdd on *counter (must be 0 at launch).
+gj_status launch_cta_batched(int64_t count, int nmax, const int32_t* n, const double* const* A,
+                             double* const* X, const int32_t* order, int32_t* counter, int pivot_mode,
+                             double tau, const CtaOut& out, cudaStream_t s);
+
+// Device-side work order: counting sort of the orders, largest first.  Writes
+// order[count]; ws must hold (kCtaMaxN + 2) int32.  Also leaves *counter = 0.
+gj_status launch_order_by_size(int64_t count, const int32_t* n, int32_t* order, int32_t* ws, int32_t* counter,
+                               cudaStream_t s);
+
+}  // namespace gj

@@ -1,0 +1,743 @@
+// k_blocked.cu -- Gauss-Jordan for large n: blocked (panel + rank-b update) and unblocked.
+//
+// Blocked form (partial or no pivoting).  Applying eqs. 14-15 for the b steps of a
+// panel P = columns k0..k0+b-1 only changes the panel columns among themselves, so
+// the panel can be reduced first on its own (n x b, held in the shared memory of a
+// thread-block cluster) and the b steps applied to every other column afterwards as
+// one product.  With p the b pivot rows, M = W[p, P] and N = W[others, P] before the
+// panel, the panel ends as W[p, P] = M^-1 and W[others, P] = -N M^-1 (compact storage
+// of the D columns), and every other column R must become
+//     W[p, R] <- M^-1 W[p, R],     W[others, R] <- W[others, R] - N M^-1 W[p, R].
+// Both are one update W[:, R] += L U with U = W[p, R] taken before the update and
+// L = W[:, P] after the panel except that 1 is subtracted at the pivot entries
+// (so the pivot rows get (M^-1 - I) U + U = M^-1 U).  U is stored with zero columns on
+// P, which leaves the panel columns unchanged by the same update.
+//
+// Interchanges are implicit (positions, as in the single-CTA kernel); at the end the
+// inverse is gathered as X[i, j] = W[rowat[i], posrow[j]] (reverse-order
+// un-permutation of observation 3; no column interchanges in partial pivoting).
+//
+// Unblocked form (any pivoting, used for full pivoting at n > 128): one launch picks
+// the pivot and stages the eq. 14 row and the eq. 15 column, a second launch updates
+// the whole array and scans the next step's candidates.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "gj_paths.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gj {
+namespace {
+
+constexpr int kPanelMaxB = 64;
+constexpr int kPanelThreads = 512;
+constexpr int kPanelWarps = kPanelThreads / 32;
+
+// One pivot candidate as pushed by a cluster CTA to every CTA of the cluster.
+struct __align__(16) PanelCand {
+  uint64_t absv;                // |value| bits (pivot key)
+  int key;                      // position of the candidate row
+  int row;                      // its row index
+  double q;                     // the candidate value (the pivot if it wins)
+  double inv_q;                 // 1 / q
+  double prow[kPanelMaxB];      // eq. 14 row over the panel: row * inv_q, inv_q in the pivot slot
+};
+
+struct PanelSmem {
+  static size_t bytes(int cs, int rp, int bb) {
+    size_t s = sizeof(PanelCand) * (size_t)(2 * cs + 1);
+    s += sizeof(double) * (size_t)rp * bb;
+    s += sizeof(int) * (size_t)rp;
+    return (s + 15) & ~size_t(15);
+  }
+};
+
+__device__ __forceinline__ void consider3(double v, int key, int il, uint64_t& bv, int& bk, int& bi) {
+  const uint64_t a = abs_bits(v);
+  if (key_better(a, key, bv, bk)) {
+    bv = a;
+    bk = key;
+    bi = il;
+  }
+}
+
+__device__ __forceinline__ void warp_argmax3(uint64_t& v, int& key, int& il) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int ok = __shfl_xor_sync(0xffffffffu, key, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, il, off);
+    if (key_better(ov, ok, v, key)) {
+      v = ov;
+      key = ok;
+      il = oi;
+    }
+  }
+}
+
+// Panel of columns [k0, k0+bb) over all n rows, one cluster of `cs` CTAs; CTA r owns
+// rows [r*rp, r*rp + rp).  One cluster barrier per step: after it every CTA holds all
+// candidates of the step (pushed into its shared memory) and picks the same winner.
+__global__ void __launch_bounds__(kPanelThreads, 1)
+    panel_kernel(int n, int k0, int bb, int rp, double* __restrict__ W, int* __restrict__ posrow,
+                 double* __restrict__ Lbuf, int* __restrict__ prow_ids, double* __restrict__ pivots,
+                 int* __restrict__ piv_rows, int32_t* status, int64_t* fail_step, int mode, double tau) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int cs = (int)cluster.num_blocks();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  extern __shared__ __align__(16) char smem[];
+  PanelCand* slots = reinterpret_cast<PanelCand*>(smem);  // [2][cs]
+  PanelCand* stage = slots + 2 * cs;
+  double* Wp = reinterpret_cast<double*>(stage + 1);       // [bb][rp], column-major over own rows
+  int* posl = reinterpret_cast<int*>(Wp + (size_t)rp * bb);
+  __shared__ uint64_t red_v[kPanelWarps];
+  __shared__ int red_k[kPanelWarps], red_i[kPanelWarps];
+
+  if (*status != GJ_OK) return;  // an earlier step failed (uniform over the cluster)
+
+  const int row0 = rank * rp;
+  const int nrows = max(0, min(rp, n - row0));
+
+  for (int il = tid; il < rp; il += kPanelThreads) posl[il] = (il < nrows) ? posrow[row0 + il] : 0x7fffffff;
+  for (int e = tid; e < rp * bb; e += kPanelThreads) {
+    const int j = e / rp, il = e - j * rp;
+    Wp[il + j * rp] = (il < nrows) ? W[(int64_t)(row0 + il) + (int64_t)(k0 + j) * n] : 0.0;
+  }
+  cluster.sync();  // every CTA of the cluster is running before any remote store
+
+  // Candidate of column t at step k among the own rows; staged and pushed to all CTAs.
+  auto push_candidate = [&](int t, int k, int par) {
+    uint64_t bv = 0;
+    int bk = kNoKey, bi = -1;
+    for (int il = tid; il < nrows; il += kPanelThreads) {
+      const int p = posl[il];
+      if (mode == GJ_PIVOT_NONE) {
+        if (p == k) consider3(Wp[il + t * rp], p, il, bv, bk, bi);
+      } else if (p >= k) {
+        consider3(Wp[il + t * rp], p, il, bv, bk, bi);
+      }
+    }
+    warp_argmax3(bv, bk, bi);
+    if (lane == 0) {
+      red_v[wid] = bv;
+      red_k[wid] = bk;
+      red_i[wid] = bi;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t v = 0;
+      int key = kNoKey, il = -1;
+      for (int w = 0; w < kPanelWarps; ++w)
+        if (key_better(red_v[w], red_k[w], v, key)) {
+          v = red_v[w];
+          key = red_k[w];
+          il = red_i[w];
+        }
+      double q = 0.0, inv_q = 0.0;
+      if (il >= 0) {
+        q = Wp[il + t * rp];
+        if (lane == 0) inv_q = 1.0 / q;
+        inv_q = __shfl_sync(0xffffffffu, inv_q, 0);
+        for (int j = lane; j < bb; j += 32) stage->prow[j] = (j == t) ? inv_q : Wp[il + j * rp] * inv_q;
+      }
+      if (lane == 0) {
+        stage->absv = v;
+        stage->key = key;
+        stage->row = (il >= 0) ? row0 + il : -1;
+        stage->q = q;
+        stage->inv_q = inv_q;
+      }
+    }
+    __syncthreads();
+    // warp w copies the staged record into CTA w's slot[par][rank]
+    if (wid < cs) {
+      PanelCand* dst = cluster.map_shared_rank(&slots[par * cs + rank], wid);
+      const int4* src4 = reinterpret_cast<const int4*>(stage);
+      int4* dst4 = reinterpret_cast<int4*>(dst);
+      constexpr int kWords = sizeof(PanelCand) / sizeof(int4);
+      for (int w = lane; w < kWords; w += 32) dst4[w] = src4[w];
+    }
+    cluster.sync();
+  };
+
+  push_candidate(0, k0, 0);
+
+  int failed = 0;
+  for (int t = 0; t < bb; ++t) {
+    const int k = k0 + t;
+    const int par = t & 1;
+    // every thread takes the same winner from the local copies of all candidates
+    const PanelCand* sl = &slots[par * cs];
+    int ws = 0;
+    for (int c2 = 1; c2 < cs; ++c2)
+      if (key_better(sl[c2].absv, sl[c2].key, sl[ws].absv, sl[ws].key)) ws = c2;
+    const PanelCand& win = sl[ws];
+    int st = GJ_OK;
+    if (win.row < 0) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+    else if (win.absv >= kInfBits) st = GJ_NONFINITE;
+    else if (__longlong_as_double((long long)win.absv) <= tau) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+    if (st != GJ_OK) {
+      if (rank == 0 && tid == 0) {
+        *status = st;
+        *fail_step = k;
+      }
+      failed = 1;
+      break;
+    }
+    const int rpos = win.key, R = win.row;
+    if (rank == 0 && tid == 0) {
+      pivots[k] = win.q;
+      piv_rows[k] = rpos;
+      prow_ids[t] = R;
+    }
+    // interchange (positions), eq. 14 for the pivot row, eq. 15 for the others
+    for (int il = tid; il < nrows; il += kPanelThreads) {
+      const int grow = row0 + il;
+      int p = posl[il];
+      if (grow == R) {
+        p = k;
+        for (int j = 0; j < bb; ++j) Wp[il + j * rp] = win.prow[j];
+      } else {
+        if (p == k) p = rpos;
+        const double l = Wp[il + t * rp];
+        for (int j = 0; j < bb; ++j) {
+          const double base = (j == t) ? 0.0 : Wp[il + j * rp];
+          Wp[il + j * rp] = fma(-l, win.prow[j], base);
+        }
+      }
+      posl[il] = p;
+    }
+    __syncthreads();
+    if (t + 1 < bb) push_candidate(t + 1, k + 1, par ^ 1);
+  }
+
+  if (!failed) {
+    for (int e = tid; e < rp * bb; e += kPanelThreads) {
+      const int j = e / rp, il = e - j * rp;
+      if (il < nrows) {
+        const double v = Wp[il + j * rp];
+        W[(int64_t)(row0 + il) + (int64_t)(k0 + j) * n] = v;
+        Lbuf[(int64_t)(row0 + il) + (int64_t)j * n] = (posl[il] == k0 + j) ? v - 1.0 : v;
+      }
+    }
+    for (int il = tid; il < nrows; il += kPanelThreads) posrow[row0 + il] = posl[il];
+  }
+}
+
+// U[t, j] = W[prow_ids[t], j] for j outside the panel, 0 inside (b x n, column-major).
+__global__ void gather_u_kernel(int n, int k0, int bb, const double* __restrict__ W, const int* __restrict__ prow_ids,
+                                double* __restrict__ U, const int32_t* status) {
+  if (*status != GJ_OK) return;
+  const int64_t total = (int64_t)bb * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / bb), t = (int)(e - (int64_t)j * bb);
+    U[e] = (j >= k0 && j < k0 + bb) ? 0.0 : W[(int64_t)prow_ids[t] + (int64_t)j * n];
+  }
+}
+
+// W[:, :] += L U in FP64 (one FMA per term).  64 x 64 tile per CTA, 4 x 4 per thread.
+constexpr int kTM = 64, kTN = 64, kTK = 32;
+__global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, const double* __restrict__ L,
+                                                          const double* __restrict__ U, double* __restrict__ W,
+                                                          const int32_t* status) {
+  if (*status != GJ_OK) return;
+  __shared__ double Ls[kTK][kTM];
+  __shared__ double Us[kTK][kTN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * kTM, c0 = blockIdx.y * kTN;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int t0 = 0; t0 < bb; t0 += kTK) {
+    const int tk = min(kTK, bb - t0);
+    for (int e = tid; e < kTK * kTM; e += 256) {
+      const int t = e / kTM, r = e - t * kTM;
+      Ls[t][r] = (t < tk && m0 + r < n) ? L[(int64_t)(m0 + r) + (int64_t)(t0 + t) * n] : 0.0;
+    }
+    for (int e = tid; e < kTK * kTN; e += 256) {
+      const int c = e / kTK, t = e - c * kTK;
+      Us[t][c] = (t < tk && c0 + c < n) ? U[(int64_t)(t0 + t) + (int64_t)(c0 + c) * bb] : 0.0;
+    }
+    __syncthreads();
+    for (int t = 0; t < tk; ++t) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Ls[t][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Us[t][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = c0 + ty + 16 * j;
+    if (c >= n) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + tx + 16 * i;
+      if (r < n) {
+        double* p = &W[(int64_t)r + (int64_t)c * n];
+        *p = *p + acc[i][j];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ shared epilogues
+
+__global__ void init_positions_kernel(int n, int* posrow, int* poscol, int* rowat, int* colat) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (posrow) posrow[i] = i;
+    if (poscol) poscol[i] = i;
+    if (rowat) rowat[i] = i;
+    if (colat) colat[i] = i;
+  }
+}
+
+__global__ void copy_in_kernel(int n, const double* __restrict__ A, int64_t lda, double* __restrict__ W) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, i = e - j * n;
+    W[e] = A[i + j * lda];
+  }
+}
+
+__global__ void rowat_from_posrow_kernel(int n, const int* __restrict__ posrow, int* __restrict__ rowat,
+                                         const int32_t* status) {
+  if (*status != GJ_OK) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) rowat[posrow[i]] = i;
+}
+
+// X[i, j] = W[rowat[poscol[i]], colat[posrow[j]]]  (colat / poscol null = identity)
+__global__ void unpermute_kernel(int n, const double* __restrict__ W, const int* __restrict__ rowat,
+                                 const int* __restrict__ posrow, const int* __restrict__ colat,
+                                 const int* __restrict__ poscol, double* __restrict__ X, const int32_t* status) {
+  if (*status != GJ_OK) return;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
+    const int src_r = rowat[poscol ? poscol[i] : i];
+    const int src_c = colat ? colat[posrow[j]] : posrow[j];
+    X[e] = W[(int64_t)src_r + (int64_t)src_c * n];
+  }
+}
+
+// eq. 13: sign and log2|det| from the recorded pivots and interchanges.
+__global__ void __launch_bounds__(1024) det_kernel(int n, const double* __restrict__ pivots,
+                                                   const int* __restrict__ piv_rows, const int* __restrict__ piv_cols,
+                                                   int32_t* status, int8_t* det_sign, double* det_log2,
+                                                   int64_t* fail_step) {
+  __shared__ double part[32];
+  const int tid = threadIdx.x;
+  const int ok = (*status == GJ_OK);
+  double lg = 0.0;
+  int flips = 0;
+  if (ok)
+    for (int k = tid; k < n; k += blockDim.x) {
+      lg += log2(fabs(pivots[k]));
+      flips += (pivots[k] < 0.0) + (piv_rows[k] != k) + (piv_cols ? (piv_cols[k] != k) : 0);
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lg += __shfl_xor_sync(0xffffffffu, lg, off);
+    flips += __shfl_xor_sync(0xffffffffu, flips, off);
+  }
+  __shared__ int fl[32];
+  if ((tid & 31) == 0) {
+    part[tid >> 5] = lg;
+    fl[tid >> 5] = flips;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int nw = blockDim.x >> 5;
+    lg = (tid < nw) ? part[tid] : 0.0;
+    flips = (tid < nw) ? fl[tid] : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      lg += __shfl_xor_sync(0xffffffffu, lg, off);
+      flips += __shfl_xor_sync(0xffffffffu, flips, off);
+    }
+    if (tid == 0) {
+      if (det_sign) *det_sign = ok ? ((flips & 1) ? -1 : 1) : 0;
+      if (det_log2) *det_log2 = ok ? lg : -INFINITY;
+      if (ok && fail_step) *fail_step = -1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ unblocked path
+
+struct StepState {
+  int R, C;
+  double inv_q;
+};
+
+// Initial candidate scan of A (step 0), one partial result per block.
+__global__ void __launch_bounds__(256) scan0_kernel(int n, const double* __restrict__ W, int mode,
+                                                    uint64_t* cand_v, int* cand_k) {
+  uint64_t bv = 0;
+  int bk = kNoKey;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
+    if (mode == GJ_PIVOT_PARTIAL && j != 0) continue;
+    if (mode == GJ_PIVOT_NONE && !(i == 0 && j == 0)) continue;
+    const uint64_t a = abs_bits(W[e]);
+    const int key = (mode == GJ_PIVOT_FULL) ? j * n + i : i;
+    if (key_better(a, key, bv, bk)) {
+      bv = a;
+      bk = key;
+    }
+  }
+  warp_argmax(bv, bk);
+  __shared__ uint64_t sv[8];
+  __shared__ int sk[8];
+  if ((threadIdx.x & 31) == 0) {
+    sv[threadIdx.x >> 5] = bv;
+    sk[threadIdx.x >> 5] = bk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w)
+      if (key_better(sv[w], sk[w], bv, bk)) {
+        bv = sv[w];
+        bk = sk[w];
+      }
+    cand_v[blockIdx.x] = bv;
+    cand_k[blockIdx.x] = bk;
+  }
+}
+
+__global__ void __launch_bounds__(1024) decide_kernel(int n, int k, int G, const uint64_t* cand_v, const int* cand_k,
+                                                      const double* __restrict__ W, int* rowat, int* colat,
+                                                      int* posrow, int* poscol, double* prow, double* lcol,
+                                                      StepState* ss, double* pivots, int* piv_rows, int* piv_cols,
+                                                      int32_t* status, int64_t* fail_step, int mode, double tau) {
+  if (*status != GJ_OK) return;
+  __shared__ uint64_t sv[32];
+  __shared__ int sk[32];
+  __shared__ int s_ok, s_R, s_C;
+  __shared__ double s_inv;
+  uint64_t bv = 0;
+  int bk = kNoKey;
+  for (int g = threadIdx.x; g < G; g += blockDim.x)
+    if (key_better(cand_v[g], cand_k[g], bv, bk)) {
+      bv = cand_v[g];
+      bk = cand_k[g];
+    }
+  warp_argmax(bv, bk);
+  if ((threadIdx.x & 31) == 0) {
+    sv[threadIdx.x >> 5] = bv;
+    sk[threadIdx.x >> 5] = bk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int w = 1; w < nw; ++w)
+      if (key_better(sv[w], sk[w], bv, bk)) {
+        bv = sv[w];
+        bk = sk[w];
+      }
+    int rp = k, cp = k;
+    if (mode == GJ_PIVOT_PARTIAL) rp = bk;
+    else if (mode == GJ_PIVOT_FULL) {
+      cp = bk / n;
+      rp = bk - cp * n;
+    }
+    int st = GJ_OK;
+    if (bk == kNoKey) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+    else if (bv >= kInfBits) st = GJ_NONFINITE;
+    else if (__longlong_as_double((long long)bv) <= tau) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+    if (st != GJ_OK) {
+      *status = st;
+      *fail_step = k;
+      s_ok = 0;
+    } else {
+      const int ra = rowat[k], rb = rowat[rp];
+      rowat[k] = rb;
+      rowat[rp] = ra;
+      posrow[rb] = k;
+      posrow[ra] = rp;
+      const int ca = colat[k], cb = colat[cp];
+      colat[k] = cb;
+      colat[cp] = ca;
+      poscol[cb] = k;
+      poscol[ca] = cp;
+      const double q = W[(int64_t)rb + (int64_t)cb * n];
+      pivots[k] = q;
+      piv_rows[k] = rp;
+      piv_cols[k] = cp;
+      s_ok = 1;
+      s_R = rb;
+      s_C = cb;
+      s_inv = 1.0 / q;
+      ss->R = rb;
+      ss->C = cb;
+      ss->inv_q = s_inv;
+    }
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const int R = s_R, C = s_C;
+  const double inv_q = s_inv;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    prow[j] = (j == C) ? inv_q : W[(int64_t)R + (int64_t)j * n] * inv_q;
+    lcol[j] = (j == R) ? 0.0 : W[(int64_t)j + (int64_t)C * n];
+  }
+}
+
+__global__ void __launch_bounds__(256) rank1_kernel(int n, int k, double* __restrict__ W,
+                                                    const double* __restrict__ prow, const double* __restrict__ lcol,
+                                                    const StepState* ss, const int* __restrict__ posrow,
+                                                    const int* __restrict__ poscol, uint64_t* cand_v, int* cand_k,
+                                                    const int32_t* status, int mode) {
+  if (*status != GJ_OK) return;
+  const int R = ss->R, C = ss->C;
+  const int kn = k + 1;
+  const bool search = kn < n;
+  uint64_t bv = 0;
+  int bk = kNoKey;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
+    double nv;
+    if (i == R) {
+      nv = prow[j];
+    } else {
+      const double base = (j == C) ? 0.0 : W[e];
+      nv = fma(-lcol[i], prow[j], base);
+    }
+    W[e] = nv;
+    if (search) {
+      const int pr = posrow[i];
+      if (mode == GJ_PIVOT_PARTIAL) {
+        if (j == kn && pr >= kn && key_better(abs_bits(nv), pr, bv, bk)) {
+          bv = abs_bits(nv);
+          bk = pr;
+        }
+      } else if (mode == GJ_PIVOT_FULL) {
+        const int pc = poscol[j];
+        if (pr >= kn && pc >= kn) {
+          const int key = pc * n + pr;
+          if (key_better(abs_bits(nv), key, bv, bk)) {
+            bv = abs_bits(nv);
+            bk = key;
+          }
+        }
+      } else if (pr == kn && poscol[j] == kn) {
+        bv = abs_bits(nv);
+        bk = kn;
+      }
+    }
+  }
+  warp_argmax(bv, bk);
+  __shared__ uint64_t sv[8];
+  __shared__ int sk[8];
+  if ((threadIdx.x & 31) == 0) {
+    sv[threadIdx.x >> 5] = bv;
+    sk[threadIdx.x >> 5] = bk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w)
+      if (key_better(sv[w], sk[w], bv, bk)) {
+        bv = sv[w];
+        bk = sk[w];
+      }
+    cand_v[blockIdx.x] = bv;
+    cand_k[blockIdx.x] = bk;
+  }
+}
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+template <class T>
+gj_status ws_alloc(T** p, size_t count, cudaStream_t s, void** list, int& nlist) {
+  void* q = nullptr;
+  cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count > 0 ? count : 1), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GJ_ERR_NOMEM;
+  }
+  list[nlist++] = q;
+  *p = static_cast<T*>(q);
+  return GJ_OK;
+}
+
+struct WsList {
+  void* p[16];
+  int n = 0;
+  cudaStream_t s;
+  explicit WsList(cudaStream_t st) : s(st) {}
+  ~WsList() {
+    for (int i = 0; i < n; ++i) cudaFreeAsync(p[i], s);
+  }
+};
+
+#define GJ_WS(ptr, count)                                   \
+  do {                                                      \
+    gj_status st_ = ws_alloc(&(ptr), (count), s, ws.p, ws.n); \
+    if (st_ != GJ_OK) return st_;                           \
+  } while (0)
+
+}  // namespace
+
+// Choose the cluster size and panel width for order n; returns the shared memory bytes.
+static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* rp_out) {
+  int cs = (int)((n + 255) / 256);
+  if (cs < 1) cs = 1;
+  if (cs > 16) cs = 16;
+  const size_t limit = 220 * 1024;
+  int b = want_b > 0 ? want_b : 32;
+  if (b > kPanelMaxB) b = kPanelMaxB;
+  for (;;) {
+    const int rp = (int)((n + cs - 1) / cs);
+    const size_t bytes = PanelSmem::bytes(cs, rp, b);
+    if (bytes <= limit || b <= 4) {
+      *cs_out = cs;
+      *b_out = b;
+      *rp_out = rp;
+      return bytes;
+    }
+    b /= 2;
+  }
+}
+
+gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int pivot_mode, double tau, int panel,
+                      int update, const CtaOut& out, cudaStream_t s) {
+  (void)update;
+  if (n64 > 46340) return GJ_ERR_UNSUPPORTED;
+  const int n = (int)n64;
+  int cs = 1, b = 32, rp = n;
+  const size_t smem = choose_panel(n, panel, &cs, &b, &rp);
+
+  WsList ws(s);
+  double *W, *Lbuf, *U, *pivots = out.pivots;
+  int *posrow, *rowat, *prow_ids, *piv_rows = out.piv_rows;
+  GJ_WS(W, (size_t)n * n);
+  GJ_WS(Lbuf, (size_t)n * b);
+  GJ_WS(U, (size_t)n * b);
+  GJ_WS(posrow, (size_t)n);
+  GJ_WS(rowat, (size_t)n);
+  GJ_WS(prow_ids, (size_t)b);
+  if (!pivots) GJ_WS(pivots, (size_t)n);
+  if (!piv_rows) GJ_WS(piv_rows, (size_t)n);
+
+  const int sms = num_sms();
+  copy_in_kernel<<<sms * 8, 256, 0, s>>>(n, A, lda, W);
+  GJ_CUDA(cudaGetLastError());
+  init_positions_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, posrow, nullptr, nullptr, nullptr);
+  GJ_CUDA(cudaGetLastError());
+
+  GJ_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (cs > 8) GJ_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cs, 1, 1);
+  cfg.blockDim = dim3(kPanelThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  GJ_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, panel_kernel, &cfg));
+  if (nclusters < 1) return GJ_ERR_UNSUPPORTED;
+
+  for (int k0 = 0; k0 < n; k0 += b) {
+    const int bb = (n - k0 < b) ? n - k0 : b;
+    {
+      ProfScope ps(s, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
+      GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, prow_ids, pivots, piv_rows,
+                                 out.status, out.fail_step, pivot_mode, tau));
+    }
+    prof_count(1);
+    if (bb == n) continue;  // a single panel covers every column: nothing outside it
+    int64_t gblocks = ((int64_t)bb * n + 255) / 256;
+    if (gblocks > sms * 16) gblocks = sms * 16;
+    gather_u_kernel<<<(unsigned)gblocks, 256, 0, s>>>(n, k0, bb, W, prow_ids, U, out.status);
+    GJ_CUDA(cudaGetLastError());
+    dim3 grid((n + kTM - 1) / kTM, (n + kTN - 1) / kTN);
+    {
+      // algorithmic work: the n x (n - bb) columns outside the panel, 2 bb FLOP each;
+      // bytes: W read and written once, L and U read once
+      ProfScope ps(s, "update_dfma", 2.0 * n * (double)(n - bb) * bb, 16.0 * n * (double)n + 16.0 * n * bb);
+      update_dfma_kernel<<<grid, 256, 0, s>>>(n, bb, Lbuf, U, W, out.status);
+    }
+    GJ_CUDA(cudaGetLastError());
+    prof_count(2);
+  }
+  prof_count(5);
+  rowat_from_posrow_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, posrow, rowat, out.status);
+  GJ_CUDA(cudaGetLastError());
+  unpermute_kernel<<<sms * 8, 256, 0, s>>>(n, W, rowat, posrow, nullptr, nullptr, X, out.status);
+  GJ_CUDA(cudaGetLastError());
+  det_kernel<<<1, 1024, 0, s>>>(n, pivots, piv_rows, nullptr, out.status, out.det_sign, out.det_log2, out.fail_step);
+  GJ_CUDA(cudaGetLastError());
+  return GJ_OK;
+}
+
+gj_status run_unblocked(int64_t n64, const double* A, int64_t lda, double* X, int pivot_mode, double tau,
+                        const CtaOut& out, cudaStream_t s) {
+  if (n64 > 46340) return GJ_ERR_UNSUPPORTED;
+  const int n = (int)n64;
+  WsList ws(s);
+  double *W, *prow, *lcol, *pivots = out.pivots;
+  int *posrow, *poscol, *rowat, *colat, *piv_rows = out.piv_rows, *piv_cols = out.piv_cols, *cand_k;
+  uint64_t* cand_v;
+  StepState* ss;
+  const int sms = num_sms();
+  const int G = sms * 4;
+  GJ_WS(W, (size_t)n * n);
+  GJ_WS(prow, (size_t)n);
+  GJ_WS(lcol, (size_t)n);
+  GJ_WS(posrow, (size_t)n);
+  GJ_WS(poscol, (size_t)n);
+  GJ_WS(rowat, (size_t)n);
+  GJ_WS(colat, (size_t)n);
+  GJ_WS(cand_v, (size_t)G);
+  GJ_WS(cand_k, (size_t)G);
+  GJ_WS(ss, 1);
+  if (!pivots) GJ_WS(pivots, (size_t)n);
+  if (!piv_rows) GJ_WS(piv_rows, (size_t)n);
+  if (!piv_cols) GJ_WS(piv_cols, (size_t)n);
+
+  copy_in_kernel<<<sms * 8, 256, 0, s>>>(n, A, lda, W);
+  GJ_CUDA(cudaGetLastError());
+  init_positions_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, posrow, poscol, rowat, colat);
+  GJ_CUDA(cudaGetLastError());
+  scan0_kernel<<<G, 256, 0, s>>>(n, W, pivot_mode, cand_v, cand_k);
+  GJ_CUDA(cudaGetLastError());
+  prof_count(3 + 2 * n + 2);
+  for (int k = 0; k < n; ++k) {
+    decide_kernel<<<1, 1024, 0, s>>>(n, k, G, cand_v, cand_k, W, rowat, colat, posrow, poscol, prow, lcol, ss, pivots,
+                                     piv_rows, piv_cols, out.status, out.fail_step, pivot_mode, tau);
+    rank1_kernel<<<G, 256, 0, s>>>(n, k, W, prow, lcol, ss, posrow, poscol, cand_v, cand_k, out.status, pivot_mode);
+  }
+  GJ_CUDA(cudaGetLastError());
+  unpermute_kernel<<<sms * 8, 256, 0, s>>>(n, W, rowat, posrow, colat, poscol, X, out.status);
+  GJ_CUDA(cudaGetLastError());
+  det_kernel<<<1, 1024, 0, s>>>(n, pivots, piv_rows, piv_cols, out.status, out.det_sign, out.det_log2,
+                                out.fail_step);
+  GJ_CUDA(cudaGetLastError());
+  return GJ_OK;
+}
+
+}  // namespace gj

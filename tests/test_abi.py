@@ -1,0 +1,95 @@
+"""The C-ABI library: builds, loads, exports every symbol its header declares, and rejects
+bad arguments before touching the GPU (these checks run without a GPU)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1401_7962_gb300 as gj
+from paper_1401_7962_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(gj_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return gj.lib()
+
+
+def test_header_declares_entry_points():
+    names = _declared_functions()
+    for must in ("gj_invert", "gj_invert_ex", "gj_invert_batched", "gj_batched_plan_create",
+                 "gj_batched_plan_execute", "gj_batched_plan_destroy", "gj_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_status_strings(lib):
+    for code in (0, 1, 2, 3, 4, -1, -2, -3, -4, -5):
+        assert gj.status_string(code)
+    assert gj.status_string(12345) == "unknown status"
+
+
+def test_argument_errors_need_no_gpu(lib):
+    L = lib
+    sgn, lg = ctypes.c_int(7), ctypes.c_double(1.0)
+    buf = np.zeros(16)
+    p = buf.ctypes.data
+    # negative order, lda < n, bad pivot mode, null pointers, in-place with lda != n
+    assert L.gj_invert(-1, p, 1, p, 1, None, None) == gj.ERR_ARG
+    assert L.gj_invert(4, p, 3, p + 8, 1, None, None) == gj.ERR_ARG
+    assert L.gj_invert(2, p, 2, p + 64, 5, None, None) == gj.ERR_ARG
+    assert L.gj_invert(2, None, 2, p, 1, None, None) == gj.ERR_ARG
+    assert L.gj_invert(2, p, 3, p, 1, None, None) == gj.ERR_ARG
+    # empty matrix: det is the empty product
+    assert L.gj_invert(0, None, 1, None, 1, ctypes.byref(sgn), ctypes.byref(lg)) == gj.OK
+    assert sgn.value == 1 and lg.value == 0.0
+    # failed calls leave det_sign = 0, det_log2 = -inf
+    assert L.gj_invert(-3, p, 1, p, 1, ctypes.byref(sgn), ctypes.byref(lg)) == gj.ERR_ARG
+    assert sgn.value == 0 and math.isinf(lg.value) and lg.value < 0
+    # options: negative tau, unknown path / update, bad panel width
+    for field, val in (("tau", -1.0), ("path", 9), ("update", 7), ("panel", 48)):
+        o = gj._Opts()
+        setattr(o, field, val)
+        assert L.gj_invert_ex(ctypes.byref(o), 2, p, 2, p + 64, 1, None, None) == gj.ERR_ARG
+    # batched: negative count, bad mode, order bound above 128
+    assert L.gj_invert_batched(-1, 0, None, None, None, 1, None, None, None, None) == gj.ERR_ARG
+    assert L.gj_invert_batched(3, 0, p, p, p, 9, p, None, None, None) == gj.ERR_ARG
+    assert L.gj_invert_batched(3, 129, p, p, p, 1, p, None, None, None) == gj.ERR_UNSUPPORTED
+    assert L.gj_invert_batched(0, 0, None, None, None, 1, None, None, None, None) == gj.OK
+    plan = ctypes.c_void_p()
+    nh = np.array([4, 200], dtype=np.int32)
+    assert L.gj_batched_plan_create(ctypes.byref(plan), 2, nh.ctypes.data, 1) == gj.ERR_UNSUPPORTED
+    assert L.gj_batched_plan_create(ctypes.byref(plan), -2, nh.ctypes.data, 1) == gj.ERR_ARG
+    assert L.gj_batched_plan_create(None, 2, nh.ctypes.data, 1) == gj.ERR_ARG
+    L.gj_batched_plan_destroy(None)
+
+
+def test_binding_checks_layout(lib):
+    A = np.zeros((3, 3))  # C-ordered: not column-major
+    with pytest.raises(ValueError):
+        gj.invert(A[:, :2])
+    with pytest.raises(ValueError):
+        gj.invert(np.ascontiguousarray(np.arange(9.0).reshape(3, 3))[:, ::-1])
+    with pytest.raises(TypeError):
+        gj.invert(np.asfortranarray(np.eye(3, dtype=np.float32)))

@@ -1,0 +1,125 @@
+"""CUDA batched inversion (persistent launch, largest-first queue, CUDA graph replay)
+against the CPU oracle, matrix by matrix, on the seeded diagonally dominant batch recipe
+(orders uniform in 4..64, entries U[-1,1], diagonal 1 + sum of the row's |off-diagonal|)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1401_7962_gb300 as gj
+from paper_1401_7962_gb300 import workloads as wl
+from tests.parity import EPS
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1401_7962_gb300 import _build
+    _build.build()
+    gj.lib()
+
+
+def to_device_batch(sizes, packed, offsets):
+    dA = torch.from_numpy(packed).cuda()
+    dX = torch.full_like(dA, float("nan"))
+    base_a, base_x = dA.data_ptr(), dX.data_ptr()
+    a_ptrs = torch.from_numpy(base_a + 8 * offsets.astype(np.int64)).cuda()
+    x_ptrs = torch.from_numpy(base_x + 8 * offsets.astype(np.int64)).cuda()
+    n_dev = torch.from_numpy(sizes.astype(np.int32)).cuda()
+    count = len(sizes)
+    st = torch.full((count,), -99, dtype=torch.int32, device="cuda")
+    sg = torch.zeros((count,), dtype=torch.int8, device="cuda")
+    lg = torch.zeros((count,), dtype=torch.float64, device="cuda")
+    return dA, dX, a_ptrs, x_ptrs, n_dev, st, sg, lg
+
+
+def compare(sizes, packed, offsets, X, st, sg, lg, idx, mode=1):
+    for m in idx:
+        n = int(sizes[m])
+        A = wl.unpack(sizes, packed, offsets, m)
+        o = oracle.invert(A, mode)
+        assert st[m] == o["status"], (m, st[m], o["status"])
+        if o["status"] != 0:
+            assert sg[m] == 0
+            continue
+        Xm = X[offsets[m]: offsets[m] + n * n].reshape(n, n, order="F")
+        assert sg[m] == o["det_sign"]
+        assert abs(lg[m] - o["det_log2"]) <= 1e-12 * max(1.0, abs(o["det_log2"]))
+        if n:
+            kappa = np.linalg.cond(A, 1)
+            assert np.max(np.abs(Xm - o["X"])) <= 64 * n * kappa * EPS * np.max(np.abs(o["X"])), m
+            R = A @ Xm - np.eye(n)
+            assert np.linalg.norm(R) / (n * np.linalg.norm(A) * np.linalg.norm(Xm)) <= 1e-14
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batched_small_all_matrices(mode):
+    sizes, packed, offsets = wl.diag_dominant_batch(600, seed=77)
+    dA, dX, ap, xp, nd, st, sg, lg = to_device_batch(sizes, packed, offsets)
+    gj.invert_batched(nd, ap, xp, st, sg, lg, pivot_mode=mode, nmax=64)
+    torch.cuda.synchronize()
+    compare(sizes, packed, offsets, dX.cpu().numpy(), st.cpu().numpy(), sg.cpu().numpy(), lg.cpu().numpy(),
+            range(len(sizes)), mode)
+
+
+def test_batched_ragged_orders_and_errors():
+    rng = np.random.default_rng(3)
+    sizes = np.array([0, 1, 2, 3, 17, 33, 64, 65, 100, 127, 128, 5, 0, 1], dtype=np.int32)
+    offsets = np.zeros(len(sizes), dtype=np.int64)
+    offsets[1:] = np.cumsum(sizes.astype(np.int64) ** 2)[:-1]
+    packed = np.zeros(int((sizes.astype(np.int64) ** 2).sum()) + 1)
+    for m, n in enumerate(sizes):
+        M = rng.standard_normal((n, n)) + n * np.eye(n)
+        packed[offsets[m]: offsets[m] + n * n] = M.reshape(-1, order="F")
+    # a singular one and a NaN one
+    packed[offsets[4]: offsets[4] + 17] = 0.0  # column 0 of the 17 x 17 matrix
+    packed[offsets[5] + 40] = np.nan
+    dA, dX, ap, xp, nd, st, sg, lg = to_device_batch(sizes, packed, offsets)
+    gj.invert_batched(nd, ap, xp, st, sg, lg, pivot_mode=1, nmax=128)
+    torch.cuda.synchronize()
+    stc = st.cpu().numpy()
+    assert stc[4] == 1 and stc[5] == 3
+    compare(sizes, packed, offsets, dX.cpu().numpy(), stc, sg.cpu().numpy(), lg.cpu().numpy(), range(len(sizes)))
+    # an order above nmax is rejected per matrix, the rest still run
+    st.fill_(-99)
+    gj.invert_batched(nd, ap, xp, st, sg, lg, pivot_mode=1, nmax=64)
+    torch.cuda.synchronize()
+    stc = st.cpu().numpy()
+    for m, n in enumerate(sizes):
+        assert stc[m] == (gj.ERR_ARG if n > 64 else (0 if m not in (4, 5) else stc[m]))
+
+
+def test_plan_graph_replay_matches_direct():
+    sizes, packed, offsets = wl.diag_dominant_batch(2000, seed=78)
+    dA, dX, ap, xp, nd, st, sg, lg = to_device_batch(sizes, packed, offsets)
+    plan = gj.BatchedPlan(sizes, gj.PIVOT_PARTIAL)
+    s = torch.cuda.Stream()
+    for use_graph in (False, True, True):
+        dX.fill_(float("nan"))
+        st.fill_(-99)
+        with torch.cuda.stream(s):
+            plan.execute(ap, xp, st, sg, lg, stream=s, use_graph=use_graph)
+        s.synchronize()
+        X = dX.cpu().numpy()
+        compare(sizes, packed, offsets, X, st.cpu().numpy(), sg.cpu().numpy(), lg.cpu().numpy(),
+                range(0, len(sizes), 7))
+        assert (st.cpu().numpy() == 0).all()
+    plan.close()
+
+
+def test_batched_200k_workload_sampled():
+    """The 200,000-matrix workload in the benchmark's launch configuration (plan + graph):
+    every status is OK and every determinant positive (strict diagonal dominance with a
+    positive diagonal implies det > 0); 300 sampled matrices are compared with the oracle."""
+    sizes, packed, offsets = wl.diag_dominant_batch(200_000, seed=wl.SEED_BASE + 3)
+    dA, dX, ap, xp, nd, st, sg, lg = to_device_batch(sizes, packed, offsets)
+    plan = gj.BatchedPlan(sizes, gj.PIVOT_PARTIAL)
+    plan.execute(ap, xp, st, sg, lg, use_graph=True)
+    torch.cuda.synchronize()
+    stc, sgc = st.cpu().numpy(), sg.cpu().numpy()
+    assert (stc == 0).all() and (sgc == 1).all()
+    rng = np.random.default_rng(1)
+    idx = rng.choice(len(sizes), 300, replace=False)
+    compare(sizes, packed, offsets, dX.cpu().numpy(), stc, sgc, lg.cpu().numpy(), idx)
+    plan.close()
