@@ -238,7 +238,10 @@ def run_gpu(args) -> None:
     import paper_1401_7962_gb300 as gj
     import ctypes
     L = gj.lib()
-    W = WORKLOADS[args.workload]
+    W = dict(WORKLOADS[args.workload])
+    if args.n and "n" in W:
+        W["n"] = args.n
+        W["name"] = W["name"].replace(str(WORKLOADS[args.workload]["n"]), str(args.n))
     stream = torch.cuda.Stream(device=dev)
     Entry = _profile_struct()[0]
     prof_entries = (Entry * 16)()
@@ -343,7 +346,7 @@ def run_gpu(args) -> None:
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
-    if rank == 0 or world > 1:
+    if (rank == 0 or world > 1) and not args.no_e2e:
         e2e = run_e2e(args, gj, L, W, stream, dev, h2d, d2h, units_step, flops_step, rank)
         if world > 1:
             e2e["value"] = e2e["value"]  # per-rank; aggregate below
@@ -353,7 +356,7 @@ def run_gpu(args) -> None:
             e2e.pop("_seconds", None)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and not args.n:
         cpu = cpu_oracle_sample(args.workload)
         cpu.pop("gflops", None)
 
@@ -468,6 +471,9 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--n", type=int, default=0,
+                    help="order of the single-matrix workload (default: the workload's own); for profiling runs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gj":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
