@@ -128,6 +128,30 @@ gj_status gj_invert_batched(int64_t count, int32_t nmax, const int32_t* n, const
                             double* const* Ainv, int pivot_mode, int32_t* status, int8_t* det_sign,
                             double* det_log2, void* stream);
 
+/*
+ * gj_invert_batched_noalloc -- gj_invert_batched without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory when they invert (code running while a stream capture is
+ * active in global mode, where cudaMalloc is illegal; real-time loops that must not
+ * take the allocator's locks or risk its latency or failure; programs that hand all
+ * device memory to their own pool).  Arguments, results and stream ordering are those
+ * of gj_invert_batched.
+ *   - Scratch (work order, histogram, queue counter) lives in a static device array of
+ *     GJ_NOALLOC_MAX_COUNT + 131 int32 (about 4 MiB) that every GPU loading the library
+ *     holds until the process exits.  count > GJ_NOALLOC_MAX_COUNT returns
+ *     GJ_ERR_UNSUPPORTED before any launch (gj_last_error() says why).
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - Every call shares the one array: calls whose execution overlaps on the GPU race
+ *     and must be serialised by the caller.  Each call clears what must start at zero.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+#define GJ_NOALLOC_MAX_COUNT 1048576
+gj_status gj_invert_batched_noalloc(int64_t count, int32_t nmax, const int32_t* n, const double* const* A,
+                                    double* const* Ainv, int pivot_mode, int32_t* status, int8_t* det_sign,
+                                    double* det_log2, void* stream);
+
 /* A batched plan fixes the orders (host copy given at creation), precomputes the
  * largest-first work order and launch shape, and can be replayed as a CUDA graph. */
 typedef struct gj_plan gj_plan;

@@ -16,7 +16,7 @@ import os
 
 from . import _build
 
-__all__ = ["lib", "invert", "invert_batched", "BatchedPlan", "GJError", "colmajor", "status_string",
+__all__ = ["lib", "invert", "invert_batched", "invert_batched_noalloc", "BatchedPlan", "GJError", "colmajor", "status_string",
            "PIVOT_NONE", "PIVOT_PARTIAL", "PIVOT_FULL"]
 
 OK, SINGULAR, ZERO_PIVOT, NONFINITE, NOT_CONVERGED = 0, 1, 2, 3, 4
@@ -58,6 +58,8 @@ def lib() -> ctypes.CDLL:
     L.gj_invert_ex.argtypes = [ctypes.POINTER(_Opts), I64, P, I64, P, I, P, P]
     L.gj_invert_batched.restype = I
     L.gj_invert_batched.argtypes = [I64, I32, P, P, P, I, P, P, P, P]
+    L.gj_invert_batched_noalloc.restype = I
+    L.gj_invert_batched_noalloc.argtypes = [I64, I32, P, P, P, I, P, P, P, P]
     L.gj_batched_plan_create.restype = I
     L.gj_batched_plan_create.argtypes = [ctypes.POINTER(P), I64, P, I]
     L.gj_batched_plan_execute.restype = I
@@ -201,6 +203,22 @@ def invert_batched(n_dev, A_ptrs, X_ptrs, status, det_sign=None, det_log2=None, 
                              _ptr(status), _ptr(det_sign), _ptr(det_log2), _stream_handle(stream))
     if st != OK:
         raise GJError(st, "gj_invert_batched")
+
+
+NOALLOC_MAX_COUNT = 1048576
+
+
+def invert_batched_noalloc(n_dev, A_ptrs, X_ptrs, status, det_sign=None, det_log2=None, *,
+                           pivot_mode: int = PIVOT_PARTIAL, nmax: int = 0, stream=None) -> None:
+    """``gj_invert_batched_noalloc``: as ``invert_batched`` but with no device allocation
+    (scratch in a static device array; at most ``NOALLOC_MAX_COUNT`` matrices; calls that
+    overlap on the GPU race and must be serialised by the caller)."""
+    L = lib()
+    count = int(n_dev.shape[0])
+    st = L.gj_invert_batched_noalloc(count, int(nmax), _ptr(n_dev), _ptr(A_ptrs), _ptr(X_ptrs), int(pivot_mode),
+                                     _ptr(status), _ptr(det_sign), _ptr(det_log2), _stream_handle(stream))
+    if st != OK:
+        raise GJError(st, "gj_invert_batched_noalloc")
 
 
 class BatchedPlan:

@@ -14,6 +14,8 @@ namespace gj {
 
 static thread_local char g_last_error[512] = "";
 
+void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 gj_status cuda_fail(cudaError_t e, const char* what) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
   return GJ_ERR_CUDA;

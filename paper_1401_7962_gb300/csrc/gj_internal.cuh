@@ -13,6 +13,9 @@ namespace gj {
 // Record a CUDA error in the thread-local last-error text; returns GJ_ERR_CUDA.
 gj_status cuda_fail(cudaError_t e, const char* what);
 
+// Set the thread-local text returned by gj_last_error().
+void set_last_error(const char* msg);
+
 #define GJ_CUDA(call)                                   \
   do {                                                  \
     cudaError_t e_ = (call);                            \

@@ -34,7 +34,7 @@ def lib():
 
 def test_header_declares_entry_points():
     names = _declared_functions()
-    for must in ("gj_invert", "gj_invert_ex", "gj_invert_batched", "gj_batched_plan_create",
+    for must in ("gj_invert", "gj_invert_ex", "gj_invert_batched", "gj_invert_batched_noalloc", "gj_batched_plan_create",
                  "gj_batched_plan_execute", "gj_batched_plan_destroy", "gj_status_string"):
         assert must in names
 
