@@ -40,6 +40,14 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Nominal GB300 FP64 rate: 152 SMs x 2 FP64 FMA lanes per clock x 2 FLOP x ~2.06 GHz.
 FP64_NOMINAL_GFLOPS = 1250.0
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel from one ncu capture (profiles/), with the order it was taken at; scaled to the
+# benchmark's order by the n^2 elements one update launch touches.  Set an entry to None
+# when its kernel changes, until it is captured again.
+NCU_TRAFFIC = {
+    "update_dfma": {"n": 6144, "bytes": 305.597184e6 + 240.446464e6},
+}
+
 WORKLOADS = {
     "inv8192": dict(n=8192, shift=0.1, pivot=1, seed=wl.SEED_BASE + 2,
                     name="gj-inverse-8192-fp64-partial-blocked"),
@@ -339,7 +347,11 @@ def run_gpu(args) -> None:
         avg_ms = d["total_ms"] / d["launches"]
         fl = d["flops"] / d["launches"] if d["flops"] else per_launch_flops
         achieved_gflops = fl / (avg_ms / 1000.0) / 1e9
-        roof = roofline_fp64(achieved_gflops, args.traffic)
+        traffic = args.traffic
+        t = NCU_TRAFFIC.get(dominant)
+        if traffic is None and t and "n" in W:
+            traffic = t["bytes"] * (W["n"] / t["n"]) ** 2
+        roof = roofline_fp64(achieved_gflops, traffic)
         roof["kernel"] = dominant
         roof["avg_launch_ms"] = round(avg_ms, 6)
         roof["share_of_step"] = round(d["total_ms"] / ms, 4)
