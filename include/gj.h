@@ -152,6 +152,24 @@ gj_status gj_invert_batched_noalloc(int64_t count, int32_t nmax, const int32_t* 
                                     double* const* Ainv, int pivot_mode, int32_t* status, int8_t* det_sign,
                                     double* det_log2, void* stream);
 
+/*
+ * gj_gemm_update_emulated -- C += L U in FP64 with the inner dimension K <= 128, computed
+ * on BF16 tcgen05 tensor cores by exact digit splitting (the kernel of the blocked path's
+ * rank-b update, the product form of eqs. 14-15 applied b steps at a time).
+ *   M, N, K    sizes, M, N >= 0, 0 <= K <= 128.
+ *   L          [ldl * K] device, column-major M x K, ldl >= M.
+ *   U          [ldu * N] device, column-major K x N, ldu >= K.
+ *   C          [ldc * N] device, column-major M x N, ldc >= M; updated in place.
+ *   slices     digits per operand entry, 1..8 (7 bits each; 7 or 8 reach FP64-level error:
+ *              truncation below 2^-7*slices relative to each row / column scale).
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * Synchronous (waits for the stream: it reports device-side wait expiry as
+ * GJ_ERR_TIMEOUT).  Uses a stream-ordered workspace of about
+ * slices * (M + N) * 256 bytes.
+ */
+gj_status gj_gemm_update_emulated(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* U,
+                                  int64_t ldu, double* C, int64_t ldc, int slices, void* stream);
+
 /* A batched plan fixes the orders (host copy given at creation), precomputes the
  * largest-first work order and launch shape, and can be replayed as a CUDA graph. */
 typedef struct gj_plan gj_plan;

@@ -60,6 +60,8 @@ def lib() -> ctypes.CDLL:
     L.gj_invert_batched.argtypes = [I64, I32, P, P, P, I, P, P, P, P]
     L.gj_invert_batched_noalloc.restype = I
     L.gj_invert_batched_noalloc.argtypes = [I64, I32, P, P, P, I, P, P, P, P]
+    L.gj_gemm_update_emulated.restype = I
+    L.gj_gemm_update_emulated.argtypes = [I64, I64, I64, P, I64, P, I64, P, I64, I, P]
     L.gj_batched_plan_create.restype = I
     L.gj_batched_plan_create.argtypes = [ctypes.POINTER(P), I64, P, I]
     L.gj_batched_plan_execute.restype = I

@@ -1,0 +1,22 @@
+// gj_ozaki.cuh -- FP64-accurate rank-k update on BF16 tensor cores (k_ozaki.cu).
+#pragma once
+
+#include "gj_internal.cuh"
+
+namespace gj {
+
+// Device workspace bytes for ozaki_update with an M x N result and S digit slices.
+size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S);
+
+// C[M x N] += L[M x K] U[K x N] (K <= 128), FP64 in and out, emulated on BF16 tcgen05 with
+// S digit slices per operand.  L is column-major (ld ldl); with l_minus_one_at, 1 is
+// subtracted from L[l_minus_one_at[k], k].  U[k, j] = U[k + j*ldu], or with u_row_ids
+// U[u_row_ids[k] + j*ldu]; columns j in [zero_lo, zero_hi) of U are taken as zero and those
+// columns of C are left untouched.  `ws` holds ozaki_workspace_bytes(M, N, S); `err`
+// receives a nonzero code if a bounded device wait expired; kernels return at once when
+// *status != GJ_OK (status may be null).
+gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
+                       const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
+                       int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s);
+
+}  // namespace gj

@@ -1,0 +1,452 @@
+// k_ozaki.cu -- FP64-accurate rank-k update C += L U (k <= 128) on BF16 tcgen05 tensor cores.
+//
+// The blocked Gauss-Jordan update is a product with a short inner dimension (the panel
+// width).  GB300's FP64 units deliver about 1.2 TFLOP/s, its BF16 tensor cores about
+// 1.9 PFLOP/s, so the update is emulated (an error-free splitting in the manner of the
+// Ozaki scheme):
+//   * every row i of L is scaled by a power of two 2^e_i with max_k |L_ik| < 2^e_i and
+//     every column j of U by 2^f_j; the scaled entries, in (-1, 1), are cut into S signed
+//     7-bit digits (magnitude 0..127, exactly representable in BF16):
+//         L_ik = 2^e_i sum_s a_s[i,k] 2^-7(s+1)   (truncated after S digits)
+//   * the digit products with s + t <= S - 1 are accumulated by the tensor cores in FP32
+//     in tensor memory, one accumulator per group g = s + t.  Each digit product is
+//     < 2^14, each pair's sum over k <= 128 terms < 2^21 and each group (<= 8 pairs)
+//     < 2^24, so every FP32 partial sum is an exact integer;
+//   * the epilogue combines the groups exactly in a 64-bit integer (weights 2^-7(g+2)),
+//     converts once to FP64, scales by 2^(e_i + f_j) and adds to C with one FP64 FMA.
+// The truncation error per entry is below 2^-7S relative to the row / column scale (S = 7:
+// 2^-49; S = 8: 2^-56), i.e. at the level of an FP64 product's rounding.
+//
+// Kernel shape: one CTA per 128 x 64 tile of C, 4 warps.  Warp 0 issues the TMA loads
+// (all S digit slices of the U tile stay resident; the L slices stream through a
+// 4-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), and all
+// four warps run the epilogue (thread = row of the tile, TMEM lane = row).  Every mbarrier
+// wait is bounded in time; on expiry the kernel records an error, drains its own TMA
+// loads and MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <mutex>
+
+#include "gj_internal.cuh"
+#include "gj_ozaki.cuh"
+#include "tc_ptx.cuh"
+
+namespace gj {
+namespace {
+
+constexpr int kTM = 128;          // tile rows (MMA M)
+constexpr int kTN = 64;           // tile columns (MMA N)
+constexpr int kKB = 128;          // slice row length in elements (max inner dimension)
+constexpr int kKC = 64;           // elements per TMA box along k (128 bytes, one swizzle row)
+constexpr int kStages = 4;        // ring of L-slice boxes
+constexpr int kABox = kTM * kKC * 2;   // 16 KiB
+constexpr int kBBox = kTN * kKC * 2;   // 8 KiB
+constexpr int kThreads = 128;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
+
+// ---------------------------------------------------------------- digit slicing
+
+__device__ __forceinline__ int exp_of(double x) {
+  // e with |x| < 2^e for normal x; -100000 for zero / subnormal (flushed)
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  return E == 0 ? -100000 : E - 1022;
+}
+
+// floor(|x| * 2^(7S - e)) for |x| < 2^e (subnormals flush to 0)
+__device__ __forceinline__ unsigned long long digits_of(double x, int e, int S) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  if (E == 0) return 0ull;
+  const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int shift = (E - 1023) - 52 + 7 * S - e;
+  if (shift >= 0) return M << shift;
+  if (shift <= -64) return 0ull;
+  return M >> (-shift);
+}
+
+__device__ __forceinline__ void write_digits(__nv_bfloat16* out, int S, int64_t slice_stride, int64_t off,
+                                             const double (&x)[4], int e) {
+  unsigned long long m[4];
+  int neg[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    m[q] = digits_of(x[q], e, S);
+    neg[q] = x[q] < 0.0;
+  }
+  for (int s = 0; s < S; ++s) {
+    const int sh = 7 * (S - 1 - s);
+    __align__(8) __nv_bfloat16 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int d = static_cast<int>((m[q] >> sh) & 0x7Full);
+      v[q] = __float2bfloat16_rn(static_cast<float>(neg[q] ? -d : d));
+    }
+    *reinterpret_cast<uint2*>(out + s * slice_stride + off) = *reinterpret_cast<const uint2*>(v);
+  }
+}
+
+// Rows of L (M x K, column-major, ld ldl) -> slices [S][mpad][128] and row exponents.
+// minus_one_at[k] (optional): subtract 1 from L[minus_one_at[k], k] (the blocked
+// Gauss-Jordan L of the panel: pivot entries minus the identity).
+__global__ void slice_rows_kernel(int M, int K, const double* __restrict__ L, int64_t ldl,
+                                  const int* __restrict__ minus_one_at, int S, int mpad,
+                                  __nv_bfloat16* __restrict__ out, int* __restrict__ erow, const int32_t* status) {
+  if (status && *status != GJ_OK) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  int mo[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = lane * 4 + q;
+    mo[q] = (minus_one_at && k < K) ? minus_one_at[k] : -1;
+  }
+  for (int i = warp; i < mpad; i += nwarps) {
+    double x[4];
+    int e = -100000;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = lane * 4 + q;
+      double v = (i < M && k < K) ? L[(int64_t)i + (int64_t)k * ldl] : 0.0;
+      if (mo[q] == i) v -= 1.0;
+      x[q] = v;
+      e = max(e, exp_of(v));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+    write_digits(out, S, (int64_t)mpad * kKB, (int64_t)i * kKB + lane * 4, x, e);
+    if (lane == 0) erow[i] = e;
+  }
+}
+
+// Columns of U (K x N) -> slices [S][npad][128] and column exponents.  U[k, j] is
+// U[k + j*ldu], or, with row_ids, W[row_ids[k] + j*ldu] (the pivot rows of a panel);
+// columns in [zero_lo, zero_hi) are zero.
+__global__ void slice_cols_kernel(int N, int K, const double* __restrict__ U, int64_t ldu,
+                                  const int* __restrict__ row_ids, int zero_lo, int zero_hi, int S, int npad,
+                                  __nv_bfloat16* __restrict__ out, int* __restrict__ ecol, const int32_t* status) {
+  if (status && *status != GJ_OK) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  int rid[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = lane * 4 + q;
+    rid[q] = (k < K) ? (row_ids ? row_ids[k] : k) : -1;
+  }
+  for (int j = warp; j < npad; j += nwarps) {
+    double x[4];
+    int e = -100000;
+    const bool live = j < N && !(j >= zero_lo && j < zero_hi);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double v = (live && rid[q] >= 0) ? U[(int64_t)rid[q] + (int64_t)j * ldu] : 0.0;
+      x[q] = v;
+      e = max(e, exp_of(v));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+    write_digits(out, S, (int64_t)npad * kKB, (int64_t)j * kKB + lane * 4, x, e);
+    if (lane == 0) ecol[j] = e;
+  }
+}
+
+// ---------------------------------------------------------------- tensor-core update
+
+struct SmemLayout {
+  static size_t bytes(int S) { return 1024 /*align slack*/ + (size_t)S * 2 * kBBox + (size_t)kStages * kABox; }
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    ozaki_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
+                        int N, int mpad, int npad, int S, int nkc, int skip_lo, int skip_hi, double* __restrict__ C,
+                        int64_t ldc, const int* __restrict__ erow, const int* __restrict__ ecol, int32_t* err,
+                        const int32_t* status) {
+  const int tn = blockIdx.x, tm = blockIdx.y;
+  const int c0 = tn * kTN, m0 = tm * kTM;
+  if (status && *status != GJ_OK) return;
+  if (c0 >= skip_lo && c0 + kTN <= skip_hi) return;  // tile inside the panel: nothing to add
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* Bres = smem;                                   // [S][nkc] boxes of 8 KiB
+  uint8_t* Aring = smem + (size_t)S * 2 * kBBox;          // [kStages] boxes of 16 KiB
+  __shared__ __align__(8) uint64_t bar_b, bar_full[kStages], bar_empty[kStages], bar_acc, bar_fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tc::mbar_init(&bar_b, 1);
+    for (int i = 0; i < kStages; ++i) {
+      tc::mbar_init(&bar_full[i], 1);
+      tc::mbar_init(&bar_empty[i], 1);
+    }
+    tc::mbar_init(&bar_acc, 1);
+    tc::mbar_init(&bar_fin, 1);
+    tc::fence_mbar_init();
+    s_abort = 0;
+    tc::tma_prefetch_desc(&mapA);
+    tc::tma_prefetch_desc(&mapB);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&s_tmem, 512);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  int issued_uses[kStages] = {0, 0, 0, 0};  // producer bookkeeping (lane 0 of warp 0)
+  bool b_issued = false;
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    tc::mbar_arrive_expect_tx(&bar_b, (uint32_t)(S * nkc * kBBox));
+    b_issued = true;
+    for (int t = 0; t < S; ++t)
+      for (int kc = 0; kc < nkc; ++kc)
+        tc::tma_load_2d(Bres + (size_t)(t * 2 + kc) * kBBox, &mapB, kc * kKC, t * npad + c0, &bar_b);
+    int it = 0;
+    for (int s = 0; s < S && !s_abort; ++s)
+      for (int kc = 0; kc < nkc; ++kc, ++it) {
+        const int stage = it % kStages, use = it / kStages;
+        if (use > 0 && !tc::mbar_wait(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
+          atomicExch(err, 1);
+          s_abort = 1;
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&bar_full[stage], (uint32_t)kABox);
+        tc::tma_load_2d(Aring + (size_t)stage * kABox, &mapA, kc * kKC, s * mpad + m0, &bar_full[stage]);
+        issued_uses[stage] = use + 1;
+      }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    bool ok = tc::mbar_wait(&bar_b, 0, kWaitNs);
+    int it = 0;
+    for (int s = 0; s < S && ok; ++s) {
+      for (int kc = 0; kc < nkc && ok; ++kc) {
+        const int stage = (it + kc) % kStages, use = (it + kc) / kStages;
+        ok = tc::mbar_wait(&bar_full[stage], (uint32_t)(use & 1), kWaitNs);
+      }
+      if (!ok) break;
+      tc::tc_fence_after();
+      for (int t = 0; s + t < S; ++t) {
+        const uint32_t d = tmem + (uint32_t)(kTN * (s + t));
+        for (int kc = 0; kc < nkc; ++kc) {
+          const uint32_t a_base = tc::smem_u32(Aring + (size_t)((it + kc) % kStages) * kABox);
+          const uint32_t b_base = tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox);
+#pragma unroll
+          for (int k16 = 0; k16 < kKC / 16; ++k16) {
+            const uint64_t ad = tc::desc_k128_sw128(a_base + 32u * k16);
+            const uint64_t bd = tc::desc_k128_sw128(b_base + 32u * k16);
+            tc::mma_bf16(d, ad, bd, kIdesc, (s > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
+          }
+        }
+      }
+      for (int kc = 0; kc < nkc; ++kc) tc::mma_commit(&bar_empty[(it + kc) % kStages]);
+      it += nkc;
+    }
+    if (!ok) {
+      atomicExch(err, 2);
+      s_abort = 1;
+    }
+    tc::mma_commit(&bar_acc);
+  }
+  // ---- epilogue: all four warps; thread = tile row, TMEM lane = row
+  const bool have_acc = tc::mbar_wait(&bar_acc, 0, kWaitNs);
+  if (!have_acc) atomicExch(err, 3);
+  tc::tc_fence_after();
+  __syncthreads();
+  const bool good = have_acc && !s_abort;
+  if (good) {
+    const int r = warp * 32 + lane;
+    const int gi = m0 + r;
+    const int er = (gi < M) ? erow[gi] : 0;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    for (int cc = 0; cc < kTN / 16; ++cc) {
+      long long T[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) T[c] = 0;
+      for (int g = 0; g < S; ++g) {
+        uint32_t v[16];
+        tc::tmem_ld16(lane_base + (uint32_t)(kTN * g + 16 * cc), v);
+        tc::tmem_ld_wait();
+        const int sh = 55 - 7 * (g + 2);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const long long G = static_cast<long long>(__float2int_rn(__uint_as_float(v[c])));
+          T[c] += (sh >= 0) ? (G << sh) : (G >> (-sh));
+        }
+      }
+      if (gi < M) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int gj = c0 + 16 * cc + c;
+          if (gj < N && !(gj >= skip_lo && gj < skip_hi) && T[c] != 0) {
+            double* p = &C[(int64_t)gi + (int64_t)gj * ldc];
+            const int e = er + ecol[gj] - 55;
+            const double d = __ll2double_rn(T[c]);
+            if (e >= -1022 && e <= 1023)
+              *p = fma(d, __longlong_as_double(static_cast<long long>(e + 1023) << 52), *p);
+            else
+              *p = *p + ldexp(d, e);
+          }
+        }
+      }
+    }
+  }
+
+  // ---- teardown: drain own async work (bounded), then free tensor memory
+  if (s_abort || !have_acc) {
+    if (warp == 0 && lane == 0) {
+      if (b_issued) tc::mbar_wait(&bar_b, 0, kWaitNs);
+      for (int st = 0; st < kStages; ++st)
+        if (issued_uses[st] > 0) tc::mbar_wait(&bar_full[st], (uint32_t)((issued_uses[st] - 1) & 1), kWaitNs);
+    }
+    if (warp == 1 && lane == 0) {
+      tc::mma_commit(&bar_fin);
+      tc::mbar_wait(&bar_fin, 0, kWaitNs);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor [rows][128] (row pitch 256 B), box {64, box_rows}, 128-byte swizzle.
+gj_status make_slice_map(CUtensorMap* map, void* base, int64_t rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_last_error("cuTensorMapEncodeTiled is not available from the driver");
+    return GJ_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)kKB, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kKB * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char msg[128];
+    snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    set_last_error(msg);
+    return GJ_ERR_CUDA;
+  }
+  return GJ_OK;
+}
+
+}  // namespace
+
+size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S) {
+  const int64_t mpad = (M + kTM - 1) / kTM * kTM, npad = (N + kTM - 1) / kTM * kTM;
+  return (size_t)S * (mpad + npad) * kKB * 2 + (size_t)(mpad + npad) * sizeof(int) + 256;
+}
+
+gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
+                       const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
+                       int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s) {
+  if (K < 1 || K > kKB || S < 1 || S > 8) return GJ_ERR_ARG;
+  const int64_t mpad = (M + kTM - 1) / kTM * kTM, npad = (N + kTM - 1) / kTM * kTM;
+  uint8_t* p = static_cast<uint8_t*>(ws);
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(p);
+  p += (size_t)S * mpad * kKB * 2;
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(p);
+  p += (size_t)S * npad * kKB * 2;
+  int* erow = reinterpret_cast<int*>(p);
+  int* ecol = erow + mpad;
+
+  int dev = 0, sms = 0;
+  GJ_CUDA(cudaGetDevice(&dev));
+  GJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int sb = (int)std::min<int64_t>((mpad + 7) / 8, (int64_t)sms * 16);
+  slice_rows_kernel<<<sb, 256, 0, s>>>((int)M, K, L, ldl, l_minus_one_at, S, (int)mpad, As, erow, status);
+  GJ_CUDA(cudaGetLastError());
+  const int sc = (int)std::min<int64_t>((npad + 7) / 8, (int64_t)sms * 16);
+  slice_cols_kernel<<<sc, 256, 0, s>>>((int)N, K, U, ldu, u_row_ids, zero_lo, zero_hi, S, (int)npad, Bs, ecol,
+                                       status);
+  GJ_CUDA(cudaGetLastError());
+  prof_count(2);
+
+  CUtensorMap mapA, mapB;
+  gj_status st = make_slice_map(&mapA, As, (int64_t)S * mpad, kTM);
+  if (st != GJ_OK) return st;
+  st = make_slice_map(&mapB, Bs, (int64_t)S * npad, kTN);
+  if (st != GJ_OK) return st;
+  const size_t smem = SmemLayout::bytes(S);
+  GJ_CUDA(cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int nkc = (K + kKC - 1) / kKC;
+  dim3 grid((unsigned)((N + kTN - 1) / kTN), (unsigned)((M + kTM - 1) / kTM));
+  {
+    ProfScope ps(s, "update_ozaki_tc", 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
+                 16.0 * (double)M * (double)N);
+    ozaki_update_kernel<<<grid, kThreads, smem, s>>>(mapA, mapB, (int)M, (int)N, (int)mpad, (int)npad, S, nkc,
+                                                    zero_lo, zero_hi, C, ldc, erow, ecol, err, status);
+  }
+  GJ_CUDA(cudaGetLastError());
+  prof_count(1);
+  return GJ_OK;
+}
+
+}  // namespace gj
+
+using namespace gj;
+
+extern "C" gj_status gj_gemm_update_emulated(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl,
+                                             const double* U, int64_t ldu, double* C, int64_t ldc, int slices,
+                                             void* stream) {
+  set_last_error("");
+  if (M < 0 || N < 0 || K < 0 || K > 128 || slices < 1 || slices > 8) return GJ_ERR_ARG;
+  if (M == 0 || N == 0 || K == 0) return GJ_OK;
+  if (ldl < M || ldu < K || ldc < M || !L || !U || !C) return GJ_ERR_ARG;
+  if (M > 0x3fffffff || N > 0x3fffffff) return GJ_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* ws = nullptr;
+  const size_t bytes = ozaki_workspace_bytes(M, N, slices) + 16;
+  cudaError_t e = cudaMallocAsync(&ws, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GJ_ERR_NOMEM;
+  }
+  int32_t* err = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(ws) + bytes - 16);
+  cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+  gj_status st = ozaki_update(M, N, (int)K, L, ldl, nullptr, U, ldu, nullptr, 0, 0, C, ldc, slices, ws, err, nullptr,
+                              s);
+  int32_t herr = 0;
+  if (st == GJ_OK) {
+    e = cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "gj_gemm_update_emulated");
+  }
+  cudaFreeAsync(ws, s);
+  if (st == GJ_OK && herr != 0) {
+    set_last_error("tensor-core update: a bounded wait expired");
+    st = GJ_ERR_TIMEOUT;
+  }
+  return st;
+}

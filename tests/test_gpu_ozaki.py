@@ -1,0 +1,88 @@
+"""The emulated FP64 rank-k update (gj_gemm_update_emulated: BF16 tcgen05 tensor cores,
+exact digit splitting) against an FP64 product computed on the host.
+
+Error bound (derived from the splitting): every entry of L is cut to S 7-bit digits of
+its row scale 2^e_i (error < 2^(e_i - 7S)), every entry of U likewise with its column
+scale 2^f_j (2 K 2^(e_i + f_j - 7S) over the k sum), the digit pairs with s + t >= S are
+dropped (fewer than S - 1 pairs of weight 2^-7(S+2) and size < 2^14 per term: < (S - 1) K
+2^(e_i + f_j - 7S)), and the kept products are summed exactly; the entry (i, j) of L U is
+therefore off by less than (S + 2) K 2^(e_i + f_j - 7S), plus the FP64 roundings of the
+int64 -> FP64 conversion and the final add (<= 4 K eps sum_k |L_ik||U_kj| + 2 eps |C_new|).
+The test checks exactly that bound.
+"""
+import numpy as np
+import pytest
+
+import paper_1401_7962_gb300 as gj
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+EPS = float(np.finfo(np.float64).eps)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1401_7962_gb300 import _build
+    _build.build()
+    gj.lib()
+
+
+def scale_exp(x, axis):
+    """e with max |x| < 2^e along `axis` (row / column scales of the splitting)."""
+    m = np.max(np.abs(x), axis=axis)
+    e = np.floor(np.log2(np.where(m > 0, m, 1.0))).astype(np.int64) + 1
+    return np.where(m > 0, e, -100000)
+
+
+def run(M, N, K, S, rng, ldl_pad=0, scale_rows=False):
+    L = rng.standard_normal((M, K))
+    if scale_rows:
+        L *= np.exp2(rng.integers(-30, 30, size=(M, 1)))
+    U = rng.standard_normal((K, N))
+    C = rng.standard_normal((M, N))
+    Lb = np.zeros((M + ldl_pad, K), order="F")
+    Lb[:M] = L
+    dL = torch.from_numpy(Lb).cuda()
+    dU = torch.from_numpy(np.asfortranarray(U)).cuda()
+    dC = torch.from_numpy(np.asfortranarray(C)).cuda()
+    L_ = gj.lib()
+    st = L_.gj_gemm_update_emulated(M, N, K, dL.data_ptr(), M + ldl_pad, dU.data_ptr(), K, dC.data_ptr(), M, S, None)
+    assert st == 0, (st, gj.last_error())
+    got = dC.cpu().numpy()
+    ref = C + L @ U
+    e = scale_exp(L, 1)[:, None]
+    f = scale_exp(U, 0)[None, :]
+    bound = (S + 2.0) * K * np.exp2((e + f - 7 * S).astype(np.float64)) + 2 * EPS * np.abs(ref) + \
+        4 * K * EPS * (np.abs(L) @ np.abs(U))
+    return got, ref, bound
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 128), (128, 64, 16), (300, 200, 100), (257, 129, 64), (5, 3, 1),
+                                   (1000, 1000, 128), (129, 65, 127)])
+@pytest.mark.parametrize("S", [7, 8])
+def test_emulated_update_within_bound(M, N, K, S):
+    rng = np.random.default_rng(M * 7 + N * 3 + K + S)
+    got, ref, bound = run(M, N, K, S, rng)
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+def test_emulated_update_scaled_rows_and_lda():
+    rng = np.random.default_rng(11)
+    got, ref, bound = run(384, 192, 128, 8, rng, ldl_pad=9, scale_rows=True)
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("S", [1, 2, 3, 4, 5])
+def test_fewer_slices_obey_their_bound(S):
+    rng = np.random.default_rng(20 + S)
+    got, ref, bound = run(256, 128, 128, S, rng)
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_emulated_update_argument_errors():
+    L_ = gj.lib()
+    assert L_.gj_gemm_update_emulated(4, 4, 129, 1, 4, 1, 129, 1, 4, 8, None) == gj.ERR_ARG
+    assert L_.gj_gemm_update_emulated(4, 4, 4, 1, 4, 1, 4, 1, 4, 9, None) == gj.ERR_ARG
+    assert L_.gj_gemm_update_emulated(4, 4, 4, 1, 3, 1, 4, 1, 4, 8, None) == gj.ERR_ARG
+    assert L_.gj_gemm_update_emulated(0, 4, 4, 0, 1, 0, 4, 0, 1, 8, None) == gj.OK
