@@ -46,6 +46,7 @@ FP64_NOMINAL_GFLOPS = 1250.0
 # when its kernel changes, until it is captured again.
 NCU_TRAFFIC = {
     "update_dfma": {"n": 6144, "bytes": 305.597184e6 + 240.446464e6},
+    "update_ozaki_tc": None,
 }
 
 WORKLOADS = {
@@ -164,6 +165,17 @@ def measured_peaks() -> dict:
         return {}
 
 
+def roofline_tensor(tensor_tflops: float, fp64_equiv_tflops: float, pairs: int, traffic) -> dict:
+    peaks = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1720.6))
+    src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"
+    return {"bound": "tensor", "achieved": round(tensor_tflops, 2), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(tensor_tflops / peak, 4), "traffic": traffic,
+            "peak_source": f"BF16 dense sustained {src} (kernel timed inside a long step)",
+            "work": f"{pairs} BF16 digit-slice products per FP64 product term (2 K FLOP each per element)",
+            "fp64_equivalent_tflops": round(fp64_equiv_tflops, 3)}
+
+
 def roofline_fp64(achieved_gflops: float, traffic) -> dict:
     # FP64 FMA is plain ALU work on GB300 (DMMA measures no faster than DFMA), so the
     # peak is the FP64 unit rate, not a tensor rate.
@@ -247,6 +259,9 @@ def run_gpu(args) -> None:
     import ctypes
     L = gj.lib()
     W = dict(WORKLOADS[args.workload])
+    if args.count and "count" in W:
+        W["count"] = args.count
+        W["name"] = W["name"].replace("200k", f"{args.count // 1000}k")
     if args.n and "n" in W:
         W["n"] = args.n
         W["name"] = W["name"].replace(str(WORKLOADS[args.workload]["n"]), str(args.n))
@@ -296,6 +311,7 @@ def run_gpu(args) -> None:
             if stc != 0:
                 raise RuntimeError(f"gj_invert_ex failed: {gj.status_string(stc)} {gj.last_error()}")
 
+        opts.slices = args.slices
         dominant = "update_dfma" if args.workload == "inv8192" else "cta_single"
         h2d = d2h = n * n * 8
 
@@ -342,7 +358,24 @@ def run_gpu(args) -> None:
         unit = "GFLOP/s"
 
     roof = None
-    if dominant in prof and prof[dominant]["launches"]:
+    if "update_ozaki_tc" in prof and prof["update_ozaki_tc"]["launches"]:
+        dominant = "update_ozaki_tc"
+    if dominant == "update_ozaki_tc":
+        d = prof[dominant]
+        avg_ms = d["total_ms"] / d["launches"]
+        S = args.slices or 8
+        pairs = S * (S + 1) // 2
+        fp64_fl = d["flops"] / d["launches"]
+        t = NCU_TRAFFIC.get(dominant)
+        traffic = args.traffic
+        if traffic is None and t and "n" in W:
+            traffic = t["bytes"] * (W["n"] / t["n"]) ** 2
+        roof = roofline_tensor(pairs * fp64_fl / (avg_ms / 1000.0) / 1e12, fp64_fl / (avg_ms / 1000.0) / 1e12, pairs,
+                               traffic)
+        roof["kernel"] = dominant
+        roof["avg_launch_ms"] = round(avg_ms, 6)
+        roof["share_of_step"] = round(d["total_ms"] / ms, 4)
+    elif dominant in prof and prof[dominant]["launches"]:
         d = prof[dominant]
         avg_ms = d["total_ms"] / d["launches"]
         fl = d["flops"] / d["launches"] if d["flops"] else per_launch_flops
@@ -368,7 +401,7 @@ def run_gpu(args) -> None:
             e2e.pop("_seconds", None)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and not args.n:
+    if rank == 0 and world == 1 and not args.no_cpu and not args.n and not args.count:
         cpu = cpu_oracle_sample(args.workload)
         cpu.pop("gflops", None)
 
@@ -378,7 +411,10 @@ def run_gpu(args) -> None:
                "128 KiB matrix is L2-resident; latency-bound single CTA (no flush)",
                "profile": prof}
         if args.workload == "inv8192":
-            cfg.update({"n": W["n"], "update": args.update, "input": "N(0,1) + 0.1 n I, seed 1403"})
+            eng = "fp64 fma" if (args.update == "dfma") else \
+                f"tensor cores: bf16 digit slices (S={args.slices or 8}), exact fp32 group sums, int64 recombination"
+            cfg.update({"n": W["n"], "update": args.update, "update_engine": eng,
+                        "input": "N(0,1) + 0.1 n I, seed 1403"})
         elif args.workload == "inv128":
             cfg.update({"n": W["n"], "input": "N(0,1), seed 1402"})
         else:
@@ -480,10 +516,13 @@ def main():
     ap.add_argument("--impl", choices=["gj", "reference"], default="gj")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="inv8192")
     ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
+    ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 8)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--count", type=int, default=0,
+                    help="matrices in the batched workload (default: the workload's own); for profiling runs")
     ap.add_argument("--n", type=int, default=0,
                     help="order of the single-matrix workload (default: the workload's own); for profiling runs")
     args = ap.parse_args()

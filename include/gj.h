@@ -71,10 +71,12 @@ typedef struct gj_opts {
   int32_t path;          /* 0 = automatic; 1 = single-CTA shared-memory kernel (n <= 128);
                             2 = blocked panel + rank-b update (partial / none pivoting);
                             3 = unblocked multi-CTA (any pivoting, any n) */
-  int32_t update;        /* blocked path rank-b update engine: 0 = automatic, 1 = FP64 DFMA,
-                            2 = FP64 emulated on BF16 tcgen05 tensor cores (split operands,
-                            exact FP32 partial sums, FP64 recombination) */
-  int32_t reserved0;
+  int32_t update;        /* blocked path rank-b update engine: 0 = automatic (tensor cores for
+                            n >= 512), 1 = FP64 FMA, 2 = FP64 emulated on BF16 tcgen05 tensor
+                            cores (digit-split operands, exact FP32 partial sums, FP64
+                            recombination; 128-column panels) */
+  int32_t slices;        /* digit slices per operand for update 2: 1..8, 0 = 8 (truncation
+                            below 2^-56 of each row / column scale) */
   int32_t* piv_rows;     /* optional out [n], host or device: row position interchanged
                             with position k at step k */
   int32_t* piv_cols;     /* optional out [n], host or device: same for columns */

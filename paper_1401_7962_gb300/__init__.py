@@ -34,7 +34,7 @@ class GJError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("tau", ctypes.c_double), ("panel", ctypes.c_int32),
-                ("path", ctypes.c_int32), ("update", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("update", ctypes.c_int32), ("slices", ctypes.c_int32),
                 ("piv_rows", ctypes.c_void_p), ("piv_cols", ctypes.c_void_p), ("pivots", ctypes.c_void_p),
                 ("fail_step", ctypes.c_void_p)]
 
@@ -146,7 +146,7 @@ def _stream_handle(stream) -> int:
 
 
 def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, path: int = PATH_AUTO,
-           panel: int = 0, update: int = UPDATE_AUTO, stream=None, record: bool = False):
+           panel: int = 0, update: int = UPDATE_AUTO, slices: int = 0, stream=None, record: bool = False):
     """Invert one square matrix with ``gj_invert_ex``.
 
     ``A`` and ``out`` may live on the host or on the device (the library stages host
@@ -169,6 +169,7 @@ def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, pa
     o.panel = int(panel)
     o.path = int(path)
     o.update = int(update)
+    o.slices = int(slices)
     rec = {}
     fs = ctypes.c_int64(-1)
     if record:

@@ -103,7 +103,7 @@ static gj_status run_single_device(const gj_opts& o, int64_t n, const double* dA
       return launch_cta_single((int)n, dA, lda, dX, pivot_mode, o.tau, out, s);
     case 2:
       if (pivot_mode == GJ_PIVOT_FULL) return GJ_ERR_UNSUPPORTED;
-      return run_blocked(n, dA, lda, dX, pivot_mode, o.tau, o.panel, o.update, out, s);
+      return run_blocked(n, dA, lda, dX, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s);
     case 3:
       return run_unblocked(n, dA, lda, dX, pivot_mode, o.tau, out, s);
     default:
@@ -148,7 +148,7 @@ gj_status gj_invert_ex(const gj_opts* opts, int64_t n, const double* A, int64_t 
   if (n < 0 || lda < (n > 0 ? n : 1)) return GJ_ERR_ARG;
   if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
   if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
-  if (o.path < 0 || o.path > 3 || o.update < 0 || o.update > 2) return GJ_ERR_ARG;
+  if (o.path < 0 || o.path > 3 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8) return GJ_ERR_ARG;
   if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
   if (n == 0) {
     if (det_sign) *det_sign = 1;
@@ -257,6 +257,8 @@ gj_status gj_invert_batched(int64_t count, int32_t nmax, const int32_t* n, const
 
 struct gj_plan {
   int64_t count = 0;
+  double flops = 0.0;  // sum of 2 n^3 (algorithmic work of one execution)
+  double bytes = 0.0;  // 16 sum n^2 (inputs read, inverses written)
   int nmax = 0;
   int pivot_mode = 1;
   int32_t* d_n = nullptr;
@@ -299,6 +301,11 @@ gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n
   std::vector<int32_t> order((size_t)count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return n_host[a] > n_host[b]; });
+  for (int64_t m = 0; m < count; ++m) {
+    const double nm = (double)n_host[m];
+    p->flops += 2.0 * nm * nm * nm;
+    p->bytes += 16.0 * nm * nm;
+  }
   cudaError_t e = cudaMalloc(&p->d_n, sizeof(int32_t) * (count > 0 ? count : 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int32_t) * (count > 0 ? count : 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(int32_t));
@@ -353,7 +360,11 @@ gj_status gj_batched_plan_execute(gj_plan* p, const double* const* A, double* co
     GJ_CUDA(cudaGraphInstantiate(&p->exec, g, 0));
     for (int i = 0; i < 6; ++i) p->key[i] = key[i];
   }
-  GJ_CUDA(cudaGraphLaunch(p->exec, s));
+  {
+    ProfScope ps(s, "cta_batched", p->flops, p->bytes);
+    GJ_CUDA(cudaGraphLaunch(p->exec, s));
+  }
+  prof_count(1);
   return GJ_OK;
 }
 

@@ -37,6 +37,11 @@ void prof_count(int launches) {
 
 ProfScope::ProfScope(cudaStream_t s, const char* name, double flops, double bytes) : s_(s), rec_(-1) {
   if (!g_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;  // no event records inside a graph capture
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   Rec r{name, nullptr, nullptr, flops, bytes};
   if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {

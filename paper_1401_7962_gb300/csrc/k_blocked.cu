@@ -23,6 +23,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include "gj_ozaki.cuh"
 #include "gj_paths.cuh"
 
 namespace cg = cooperative_groups;
@@ -226,20 +227,23 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   }
 }
 
-// U[t, j] = W[prow_ids[t], j] for j outside the panel, 0 inside (b x n, column-major).
-__global__ void gather_u_kernel(int n, int k0, int bb, const double* __restrict__ W, const int* __restrict__ prow_ids,
-                                double* __restrict__ U, const int32_t* status) {
+// U[t, j - c_lo] = W[prow_ids[t], j] for j in the column window [c_lo, c_hi) outside the
+// panel [k0, k0 + bb), 0 inside it (bb x (c_hi - c_lo), column-major).
+__global__ void gather_u_kernel(int n, int k0, int bb, int c_lo, int c_hi, const double* __restrict__ W,
+                                const int* __restrict__ prow_ids, double* __restrict__ U, const int32_t* status) {
   if (*status != GJ_OK) return;
-  const int64_t total = (int64_t)bb * n;
+  const int64_t total = (int64_t)bb * (c_hi - c_lo);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / bb), t = (int)(e - (int64_t)j * bb);
+    const int jj = (int)(e / bb), t = (int)(e - (int64_t)jj * bb);
+    const int j = c_lo + jj;
     U[e] = (j >= k0 && j < k0 + bb) ? 0.0 : W[(int64_t)prow_ids[t] + (int64_t)j * n];
   }
 }
 
-// W[:, :] += L U in FP64 (one FMA per term).  64 x 64 tile per CTA, 4 x 4 per thread.
+// W[:, c_lo:c_hi] += L U in FP64 (one FMA per term).  64 x 64 tile per CTA, 4 x 4 per thread.
 constexpr int kTM = 64, kTN = 64, kTK = 32;
-__global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, const double* __restrict__ L,
+__global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, int c_lo, int c_hi,
+                                                          const double* __restrict__ L,
                                                           const double* __restrict__ U, double* __restrict__ W,
                                                           const int32_t* status) {
   if (*status != GJ_OK) return;
@@ -247,7 +251,8 @@ __global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, const d
   __shared__ double Us[kTK][kTN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.x * kTM, c0 = blockIdx.y * kTN;
+  const int m0 = blockIdx.x * kTM, cw0 = blockIdx.y * kTN;  // cw: column within the window
+  const int wn = c_hi - c_lo;
   double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, const d
     }
     for (int e = tid; e < kTK * kTN; e += 256) {
       const int c = e / kTK, t = e - c * kTK;
-      Us[t][c] = (t < tk && c0 + c < n) ? U[(int64_t)(t0 + t) + (int64_t)(c0 + c) * bb] : 0.0;
+      Us[t][c] = (t < tk && cw0 + c < wn) ? U[(int64_t)(t0 + t) + (int64_t)(cw0 + c) * bb] : 0.0;
     }
     __syncthreads();
     for (int t = 0; t < tk; ++t) {
@@ -279,8 +284,9 @@ __global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, const d
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int c = c0 + ty + 16 * j;
-    if (c >= n) continue;
+    const int cw = cw0 + ty + 16 * j;
+    if (cw >= wn) continue;
+    const int c = c_lo + cw;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = m0 + tx + 16 * i;
@@ -290,6 +296,11 @@ __global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, const d
       }
     }
   }
+}
+
+// A bounded device wait of the tensor-core update expired: report it as the call's status.
+__global__ void fold_error_kernel(const int32_t* err, int32_t* status) {
+  if (*err != 0 && *status == GJ_OK) *status = GJ_ERR_TIMEOUT;
 }
 
 // ------------------------------------------------------------------ shared epilogues
@@ -579,7 +590,7 @@ gj_status ws_alloc(T** p, size_t count, cudaStream_t s, void** list, int& nlist)
 }
 
 struct WsList {
-  void* p[16];
+  void* p[24];
   int n = 0;
   cudaStream_t s;
   explicit WsList(cudaStream_t st) : s(st) {}
@@ -618,24 +629,38 @@ static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* 
 }
 
 gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int pivot_mode, double tau, int panel,
-                      int update, const CtaOut& out, cudaStream_t s) {
-  (void)update;
+                      int update, int slices, const CtaOut& out, cudaStream_t s) {
   if (n64 > 46340) return GJ_ERR_UNSUPPORTED;
   const int n = (int)n64;
   int cs = 1, b = 32, rp = n;
   const size_t smem = choose_panel(n, panel, &cs, &b, &rp);
+  // Outer panel width: the tensor-core update takes 128-column panels, reduced as
+  // 128 / b cluster sub-panels with FP64 updates inside the panel; the FP64 update path
+  // uses the cluster panel width directly.
+  const bool tc = (update == 2) || (update == 0 && n >= kTensorUpdateMinN);
+  const int S = slices > 0 ? slices : 8;
+  const int Bw = tc ? 128 : b;
 
   WsList ws(s);
   double *W, *Lbuf, *U, *pivots = out.pivots;
   int *posrow, *rowat, *prow_ids, *piv_rows = out.piv_rows;
+  void* oz_ws = nullptr;
+  int32_t* oz_err = nullptr;
   GJ_WS(W, (size_t)n * n);
   GJ_WS(Lbuf, (size_t)n * b);
   GJ_WS(U, (size_t)n * b);
   GJ_WS(posrow, (size_t)n);
   GJ_WS(rowat, (size_t)n);
-  GJ_WS(prow_ids, (size_t)b);
+  GJ_WS(prow_ids, (size_t)Bw);
+  GJ_WS(oz_err, 4);
+  if (tc) {
+    uint8_t* p8;
+    GJ_WS(p8, ozaki_workspace_bytes(n, n, S));
+    oz_ws = p8;
+  }
   if (!pivots) GJ_WS(pivots, (size_t)n);
   if (!piv_rows) GJ_WS(piv_rows, (size_t)n);
+  GJ_CUDA(cudaMemsetAsync(oz_err, 0, sizeof(int32_t), s));
 
   const int sms = num_sms();
   copy_in_kernel<<<sms * 8, 256, 0, s>>>(n, A, lda, W);
@@ -661,36 +686,58 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   GJ_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, panel_kernel, &cfg));
   if (nclusters < 1) return GJ_ERR_UNSUPPORTED;
 
-  for (int k0 = 0; k0 < n; k0 += b) {
-    const int bb = (n - k0 < b) ? n - k0 : b;
-    {
-      ProfScope ps(s, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
-      GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, prow_ids, pivots, piv_rows,
-                                 out.status, out.fail_step, pivot_mode, tau));
-    }
-    prof_count(1);
-    if (bb == n) continue;  // a single panel covers every column: nothing outside it
-    int64_t gblocks = ((int64_t)bb * n + 255) / 256;
+  auto fp64_update = [&](int k0, int bb, int c_lo, int c_hi, const int* pids) -> gj_status {
+    const int wn = c_hi - c_lo;
+    int64_t gblocks = ((int64_t)bb * wn + 255) / 256;
     if (gblocks > sms * 16) gblocks = sms * 16;
-    gather_u_kernel<<<(unsigned)gblocks, 256, 0, s>>>(n, k0, bb, W, prow_ids, U, out.status);
+    gather_u_kernel<<<(unsigned)gblocks, 256, 0, s>>>(n, k0, bb, c_lo, c_hi, W, pids, U, out.status);
     GJ_CUDA(cudaGetLastError());
-    dim3 grid((n + kTM - 1) / kTM, (n + kTN - 1) / kTN);
+    dim3 grid((n + kTM - 1) / kTM, (wn + kTN - 1) / kTN);
     {
-      // algorithmic work: the n x (n - bb) columns outside the panel, 2 bb FLOP each;
-      // bytes: W read and written once, L and U read once
-      ProfScope ps(s, "update_dfma", 2.0 * n * (double)(n - bb) * bb, 16.0 * n * (double)n + 16.0 * n * bb);
-      update_dfma_kernel<<<grid, 256, 0, s>>>(n, bb, Lbuf, U, W, out.status);
+      // algorithmic work: n x (wn - bb) columns outside the sub-panel, 2 bb FLOP each;
+      // bytes: those columns of W read and written once, L and U read once
+      ProfScope ps(s, "update_dfma", 2.0 * n * (double)(wn - bb) * bb, 16.0 * n * (double)wn + 16.0 * n * bb);
+      update_dfma_kernel<<<grid, 256, 0, s>>>(n, bb, c_lo, c_hi, Lbuf, U, W, out.status);
     }
     GJ_CUDA(cudaGetLastError());
     prof_count(2);
+    return GJ_OK;
+  };
+
+  for (int K0 = 0; K0 < n; K0 += Bw) {
+    const int BB = (n - K0 < Bw) ? n - K0 : Bw;
+    for (int k0 = K0; k0 < K0 + BB; k0 += b) {
+      const int bb = (K0 + BB - k0 < b) ? K0 + BB - k0 : b;
+      {
+        ProfScope ps(s, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
+        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, prow_ids + (k0 - K0), pivots,
+                                   piv_rows, out.status, out.fail_step, pivot_mode, tau));
+      }
+      prof_count(1);
+      if (BB > bb) {  // the rest of the outer panel
+        gj_status st = fp64_update(k0, bb, K0, K0 + BB, prow_ids + (k0 - K0));
+        if (st != GJ_OK) return st;
+      }
+    }
+    if (BB == n) continue;  // one panel covers every column: nothing outside it
+    if (tc) {
+      gj_status st = ozaki_update(n, n, BB, W + (size_t)K0 * n, n, prow_ids, W, n, prow_ids, K0, K0 + BB, W, n, S,
+                                  oz_ws, oz_err, out.status, s);
+      if (st != GJ_OK) return st;
+    } else {
+      gj_status st = fp64_update(K0, BB, 0, n, prow_ids);
+      if (st != GJ_OK) return st;
+    }
   }
-  prof_count(5);
+  fold_error_kernel<<<1, 1, 0, s>>>(oz_err, out.status);
+  GJ_CUDA(cudaGetLastError());
   rowat_from_posrow_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, posrow, rowat, out.status);
   GJ_CUDA(cudaGetLastError());
   unpermute_kernel<<<sms * 8, 256, 0, s>>>(n, W, rowat, posrow, nullptr, nullptr, X, out.status);
   GJ_CUDA(cudaGetLastError());
   det_kernel<<<1, 1024, 0, s>>>(n, pivots, piv_rows, nullptr, out.status, out.det_sign, out.det_log2, out.fail_step);
   GJ_CUDA(cudaGetLastError());
+  prof_count(6);
   return GJ_OK;
 }
 

@@ -29,6 +29,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "gj_internal.cuh"
@@ -42,10 +43,14 @@ constexpr int kTM = 128;          // tile rows (MMA M)
 constexpr int kTN = 64;           // tile columns (MMA N)
 constexpr int kKB = 128;          // slice row length in elements (max inner dimension)
 constexpr int kKC = 64;           // elements per TMA box along k (128 bytes, one swizzle row)
-constexpr int kStages = 4;        // ring of L-slice boxes
+constexpr int kStages = 4;        // ring of L-slice boxes (16 KiB each)
 constexpr int kABox = kTM * kKC * 2;   // 16 KiB
 constexpr int kBBox = kTN * kKC * 2;   // 8 KiB
-constexpr int kThreads = 128;
+constexpr int kEpiWarps = 8;      // two per TMEM lane quarter, each taking half of the tile's columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kEpiCols = kTN / 2;  // columns per epilogue thread
+constexpr int kCSm = kEpiCols / 2; // of those, prefetched into shared memory (the rest into registers)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
 
@@ -161,35 +166,48 @@ __global__ void slice_cols_kernel(int N, int K, const double* __restrict__ U, in
 // ---------------------------------------------------------------- tensor-core update
 
 struct SmemLayout {
-  static size_t bytes(int S) { return 1024 /*align slack*/ + (size_t)S * 2 * kBBox + (size_t)kStages * kABox; }
+  static size_t bytes(int S) {
+    return 1024 /*align slack*/ + (size_t)S * 2 * kBBox + (size_t)kStages * kABox + (size_t)2 * kCSm * kTM * 8;
+  }
 };
 
+// Persistent kernel: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// Roles: warp 0 = TMA producer (U slices of the tile, then the L slices through the
+// ring), warp 1 = MMA issuer, warps 2-9 = epilogue (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 and the column half (w - 2) / 4 of the tile).  Per tile: the MMA warp waits for the tile's U slices and for the
+// epilogue to have drained the previous tile's accumulators; the epilogue loads its 64 C
+// values per row into registers before waiting for the accumulators, so the C reads
+// overlap the MMAs; the U slices of the next tile load while the epilogue drains.
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
-                        int N, int mpad, int npad, int S, int nkc, int skip_lo, int skip_hi, double* __restrict__ C,
-                        int64_t ldc, const int* __restrict__ erow, const int* __restrict__ ecol, int32_t* err,
-                        const int32_t* status) {
-  const int tn = blockIdx.x, tm = blockIdx.y;
-  const int c0 = tn * kTN, m0 = tm * kTM;
+                        int N, int mpad, int npad, int S, int nkc, int tiles_m, int tiles_n, int ts_lo, int ts_hi,
+                        int skip_lo, int skip_hi, double* __restrict__ C, int64_t ldc, const int* __restrict__ erow,
+                        const int* __restrict__ ecol, int32_t* err, const int32_t* status) {
   if (status && *status != GJ_OK) return;
-  if (c0 >= skip_lo && c0 + kTN <= skip_hi) return;  // tile inside the panel: nothing to add
+  const int tiles_n_act = tiles_n - (ts_hi - ts_lo);
+  const int ntiles = tiles_m * tiles_n_act;
+  if ((int)blockIdx.x >= ntiles) return;
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* Bres = smem;                                   // [S][nkc] boxes of 8 KiB
+  uint8_t* Bres = smem;                                   // [S][2] boxes of 8 KiB
   uint8_t* Aring = smem + (size_t)S * 2 * kBBox;          // [kStages] boxes of 16 KiB
-  __shared__ __align__(8) uint64_t bar_b, bar_full[kStages], bar_empty[kStages], bar_acc, bar_fin;
+  double* Cs = reinterpret_cast<double*>(Aring + (size_t)kStages * kABox);  // [2 halves][kCSm][kTM]
+  __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_full[kStages], bar_empty[kStages], bar_accfull,
+      bar_accempty, bar_fin;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    tc::mbar_init(&bar_b, 1);
+    tc::mbar_init(&bar_bfull, 1);
+    tc::mbar_init(&bar_bempty, 1);
     for (int i = 0; i < kStages; ++i) {
       tc::mbar_init(&bar_full[i], 1);
       tc::mbar_init(&bar_empty[i], 1);
     }
-    tc::mbar_init(&bar_acc, 1);
+    tc::mbar_init(&bar_accfull, 1);
+    tc::mbar_init(&bar_accempty, kEpiThreads);
     tc::mbar_init(&bar_fin, 1);
     tc::fence_mbar_init();
     s_abort = 0;
@@ -205,109 +223,176 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::tc_fence_after();
   const uint32_t tmem = s_tmem;
 
-  int issued_uses[kStages] = {0, 0, 0, 0};  // producer bookkeeping (lane 0 of warp 0)
-  bool b_issued = false;
-  if (warp == 0 && lane == 0) {
-    // ---- producer
-    tc::mbar_arrive_expect_tx(&bar_b, (uint32_t)(S * nkc * kBBox));
-    b_issued = true;
-    for (int t = 0; t < S; ++t)
-      for (int kc = 0; kc < nkc; ++kc)
-        tc::tma_load_2d(Bres + (size_t)(t * 2 + kc) * kBBox, &mapB, kc * kKC, t * npad + c0, &bar_b);
-    int it = 0;
-    for (int s = 0; s < S && !s_abort; ++s)
-      for (int kc = 0; kc < nkc; ++kc, ++it) {
-        const int stage = it % kStages, use = it / kStages;
-        if (use > 0 && !tc::mbar_wait(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
-          atomicExch(err, 1);
+  auto tile_of = [&](int idx, int& m0, int& c0) {
+    const int tm = idx / tiles_n_act, tna = idx - tm * tiles_n_act;
+    const int tn = (tna < ts_lo) ? tna : tna + (ts_hi - ts_lo);
+    m0 = tm * kTM;
+    c0 = tn * kTN;
+  };
+
+  int issued_uses[kStages] = {0, 0, 0, 0};
+  int b_issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer
+      int it = 0, local = 0;
+      for (int idx = blockIdx.x; idx < ntiles && !s_abort; idx += gridDim.x, ++local) {
+        int m0, c0;
+        tile_of(idx, m0, c0);
+        if (local > 0 && !tc::mbar_wait(&bar_bempty, (uint32_t)((local - 1) & 1), kWaitNs)) {
+          atomicExch(err, 10);
           s_abort = 1;
           break;
         }
-        tc::mbar_arrive_expect_tx(&bar_full[stage], (uint32_t)kABox);
-        tc::tma_load_2d(Aring + (size_t)stage * kABox, &mapA, kc * kKC, s * mpad + m0, &bar_full[stage]);
-        issued_uses[stage] = use + 1;
+        tc::mbar_arrive_expect_tx(&bar_bfull, (uint32_t)(S * nkc * kBBox));
+        b_issued = local + 1;
+        for (int t = 0; t < S; ++t)
+          for (int kc = 0; kc < nkc; ++kc)
+            tc::tma_load_2d(Bres + (size_t)(t * 2 + kc) * kBBox, &mapB, kc * kKC, t * npad + c0, &bar_bfull);
+        bool ok = true;
+        for (int sl = 0; sl < S && ok; ++sl)
+          for (int kc = 0; kc < nkc; ++kc, ++it) {
+            const int stage = it % kStages, use = it / kStages;
+            if (use > 0 && !tc::mbar_wait(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
+              atomicExch(err, 11);
+              s_abort = 1;
+              ok = false;
+              break;
+            }
+            tc::mbar_arrive_expect_tx(&bar_full[stage], (uint32_t)kABox);
+            tc::tma_load_2d(Aring + (size_t)stage * kABox, &mapA, kc * kKC, sl * mpad + m0, &bar_full[stage]);
+            issued_uses[stage] = use + 1;
+          }
+        if (!ok) break;
       }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    bool ok = tc::mbar_wait(&bar_b, 0, kWaitNs);
-    int it = 0;
-    for (int s = 0; s < S && ok; ++s) {
-      for (int kc = 0; kc < nkc && ok; ++kc) {
-        const int stage = (it + kc) % kStages, use = (it + kc) / kStages;
-        ok = tc::mbar_wait(&bar_full[stage], (uint32_t)(use & 1), kWaitNs);
-      }
-      if (!ok) break;
-      tc::tc_fence_after();
-      for (int t = 0; s + t < S; ++t) {
-        const uint32_t d = tmem + (uint32_t)(kTN * (s + t));
-        for (int kc = 0; kc < nkc; ++kc) {
-          const uint32_t a_base = tc::smem_u32(Aring + (size_t)((it + kc) % kStages) * kABox);
-          const uint32_t b_base = tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int it = 0, local = 0;
+      for (int idx = blockIdx.x; idx < ntiles && !s_abort; idx += gridDim.x, ++local) {
+        bool ok = tc::mbar_wait(&bar_bfull, (uint32_t)(local & 1), kWaitNs);
+        if (ok && local > 0) ok = tc::mbar_wait(&bar_accempty, (uint32_t)((local - 1) & 1), kWaitNs);
+        if (!ok) {
+          atomicExch(err, 20);
+          s_abort = 1;
+          break;
+        }
+        tc::tc_fence_after();
+        for (int sl = 0; sl < S && ok; ++sl) {
+          for (int kc = 0; kc < nkc; ++kc, ++it) {
+            const int stage = it % kStages, use = it / kStages;
+            if (!tc::mbar_wait(&bar_full[stage], (uint32_t)(use & 1), kWaitNs)) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+            const uint64_t a0 = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kABox));
+            for (int t = 0; sl + t < S; ++t) {
+              const uint32_t d = tmem + (uint32_t)(kTN * (sl + t));
+              const uint64_t b0 = tc::desc_k128_sw128(tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox));
 #pragma unroll
-          for (int k16 = 0; k16 < kKC / 16; ++k16) {
-            const uint64_t ad = tc::desc_k128_sw128(a_base + 32u * k16);
-            const uint64_t bd = tc::desc_k128_sw128(b_base + 32u * k16);
-            tc::mma_bf16(d, ad, bd, kIdesc, (s > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
+              for (int k16 = 0; k16 < kKC / 16; ++k16)
+                tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar_empty[stage]);
           }
         }
-      }
-      for (int kc = 0; kc < nkc; ++kc) tc::mma_commit(&bar_empty[(it + kc) % kStages]);
-      it += nkc;
-    }
-    if (!ok) {
-      atomicExch(err, 2);
-      s_abort = 1;
-    }
-    tc::mma_commit(&bar_acc);
-  }
-  // ---- epilogue: all four warps; thread = tile row, TMEM lane = row
-  const bool have_acc = tc::mbar_wait(&bar_acc, 0, kWaitNs);
-  if (!have_acc) atomicExch(err, 3);
-  tc::tc_fence_after();
-  __syncthreads();
-  const bool good = have_acc && !s_abort;
-  if (good) {
-    const int r = warp * 32 + lane;
-    const int gi = m0 + r;
-    const int er = (gi < M) ? erow[gi] : 0;
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    for (int cc = 0; cc < kTN / 16; ++cc) {
-      long long T[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) T[c] = 0;
-      for (int g = 0; g < S; ++g) {
-        uint32_t v[16];
-        tc::tmem_ld16(lane_base + (uint32_t)(kTN * g + 16 * cc), v);
-        tc::tmem_ld_wait();
-        const int sh = 55 - 7 * (g + 2);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const long long G = static_cast<long long>(__float2int_rn(__uint_as_float(v[c])));
-          T[c] += (sh >= 0) ? (G << sh) : (G >> (-sh));
+        if (!ok) {
+          atomicExch(err, 21);
+          s_abort = 1;
+          break;
         }
+        tc::mma_commit(&bar_bempty);
+        tc::mma_commit(&bar_accfull);
       }
-      if (gi < M) {
+    }
+  } else {
+    // ---------------- epilogue (warps 2..9)
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;   // column half of the tile
+    const int r = q * 32 + lane;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16) + (uint32_t)(h * kEpiCols);
+    double* Csh = Cs + (size_t)h * kCSm * kTM;
+    int local = 0;
+    for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x, ++local) {
+      int m0, c0;
+      tile_of(idx, m0, c0);
+      c0 += h * kEpiCols;
+      const int gi = m0 + r;
+      const bool row_ok = gi < M;
+      // C for this row and column half, loaded before the accumulators are ready
+      // (overlaps the MMAs): kCSm columns into shared memory (cp.async), the rest into
+      // registers
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int gj = c0 + 16 * cc + c;
-          if (gj < N && !(gj >= skip_lo && gj < skip_hi) && T[c] != 0) {
-            double* p = &C[(int64_t)gi + (int64_t)gj * ldc];
+      for (int c = 0; c < kCSm; ++c) {
+        const int gj = c0 + c;
+        if (row_ok && gj < N) tc::cp_async8(&Csh[c * kTM + r], &C[(int64_t)gi + (int64_t)gj * ldc]);
+      }
+      tc::cp_async_commit();
+      double cv[kEpiCols - kCSm];
+#pragma unroll
+      for (int c = 0; c < kEpiCols - kCSm; ++c) {
+        const int gj = c0 + kCSm + c;
+        cv[c] = (row_ok && gj < N) ? C[(int64_t)gi + (int64_t)gj * ldc] : 0.0;
+      }
+      const int er = row_ok ? erow[gi] : 0;
+      bool ok = tc::mbar_wait(&bar_accfull, (uint32_t)(local & 1), kWaitNs);
+      ok = __all_sync(0xffffffffu, ok) && !__any_sync(0xffffffffu, s_abort != 0);
+      if (!ok) {
+        atomicExch(err, 30);
+        s_abort = 1;
+        break;
+      }
+      tc::tc_fence_after();
+      tc::cp_async_wait_all();
+#pragma unroll
+      for (int cc = 0; cc < kEpiCols / 8; ++cc) {
+        // all groups of this 8-column chunk in flight before one wait
+        uint32_t v[8][8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+          if (g < S) tc::tmem_ld8(lane_base + (uint32_t)(kTN * g + 8 * cc), v[g]);
+        tc::tmem_ld_wait();
+        long long T[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) T[c] = 0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          if (g >= S) continue;
+          const int sh = 55 - 7 * (g + 2);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const long long G = static_cast<long long>(__float2int_rn(__uint_as_float(v[g][c])));
+            T[c] += (sh >= 0) ? (G << sh) : (G >> (-sh));
+          }
+        }
+        if (row_ok) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int cl = 8 * cc + c;
+            const int gj = c0 + cl;
+            if (gj >= N || (gj >= skip_lo && gj < skip_hi) || T[c] == 0) continue;
             const int e = er + ecol[gj] - 55;
             const double d = __ll2double_rn(T[c]);
-            if (e >= -1022 && e <= 1023)
-              *p = fma(d, __longlong_as_double(static_cast<long long>(e + 1023) << 52), *p);
-            else
-              *p = *p + ldexp(d, e);
+            const double cold = (cl < kCSm) ? Csh[cl * kTM + r] : cv[cl - kCSm];
+            const double out = (e >= -1022 && e <= 1023)
+                                   ? fma(d, __longlong_as_double(static_cast<long long>(e + 1023) << 52), cold)
+                                   : cold + ldexp(d, e);
+            C[(int64_t)gi + (int64_t)gj * ldc] = out;
           }
         }
       }
+      tc::tc_fence_before();
+      tc::mbar_arrive(&bar_accempty);
     }
   }
 
-  // ---- teardown: drain own async work (bounded), then free tensor memory
-  if (s_abort || !have_acc) {
+  // ---------------- teardown: drain own async work (bounded), then free tensor memory
+  __syncthreads();
+  if (s_abort) {
     if (warp == 0 && lane == 0) {
-      if (b_issued) tc::mbar_wait(&bar_b, 0, kWaitNs);
+      if (b_issued > 0) tc::mbar_wait(&bar_bfull, (uint32_t)((b_issued - 1) & 1), kWaitNs);
       for (int st = 0; st < kStages; ++st)
         if (issued_uses[st] > 0) tc::mbar_wait(&bar_full[st], (uint32_t)((issued_uses[st] - 1) & 1), kWaitNs);
     }
@@ -401,12 +486,24 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   const size_t smem = SmemLayout::bytes(S);
   GJ_CUDA(cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int nkc = (K + kKC - 1) / kKC;
-  dim3 grid((unsigned)((N + kTN - 1) / kTN), (unsigned)((M + kTM - 1) / kTM));
+  const int tiles_m = (int)((M + kTM - 1) / kTM), tiles_n = (int)((N + kTN - 1) / kTN);
+  // column tiles lying wholly inside [zero_lo, zero_hi) receive nothing: not scheduled
+  int ts_lo = 0, ts_hi = 0;
+  if (zero_hi > zero_lo) {
+    ts_lo = (zero_lo + kTN - 1) / kTN;
+    ts_hi = (zero_hi >= N) ? tiles_n : zero_hi / kTN;
+    if (ts_hi > tiles_n) ts_hi = tiles_n;
+    if (ts_hi < ts_lo) ts_hi = ts_lo;
+  }
+  const int ntiles = tiles_m * (tiles_n - (ts_hi - ts_lo));
+  if (ntiles <= 0) return GJ_OK;
+  const int grid = std::min(ntiles, sms);
   {
     ProfScope ps(s, "update_ozaki_tc", 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
                  16.0 * (double)M * (double)N);
     ozaki_update_kernel<<<grid, kThreads, smem, s>>>(mapA, mapB, (int)M, (int)N, (int)mpad, (int)npad, S, nkc,
-                                                    zero_lo, zero_hi, C, ldc, erow, ecol, err, status);
+                                                    tiles_m, tiles_n, ts_lo, ts_hi, zero_lo, zero_hi, C, ldc, erow,
+                                                    ecol, err, status);
   }
   GJ_CUDA(cudaGetLastError());
   prof_count(1);

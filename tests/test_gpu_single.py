@@ -76,11 +76,22 @@ def test_cta_random(n, mode):
     assert_matches_oracle(A, r, o, mode)
 
 
+@pytest.mark.parametrize("update", [gj.UPDATE_DFMA, gj.UPDATE_TC_OZAKI])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n,panel", [(2, 16), (129, 16), (200, 32), (257, 64), (300, 0), (700, 32), (1031, 16)])
-def test_blocked_random(n, panel, mode):
+def test_blocked_random(n, panel, mode, update):
     seed, A, o = tie_free_seed(make_input(n, mode, 0), 2000 + n, mode)
-    r = run(A, mode, path=gj.PATH_BLOCKED, panel=panel)
+    r = run(A, mode, path=gj.PATH_BLOCKED, panel=panel, update=update)
+    assert_matches_oracle(A, r, o, mode)
+
+
+@pytest.mark.parametrize("slices", [7, 8])
+def test_blocked_tensor_update_slices(slices):
+    """7 digit slices (49 bits) still meet the parity bar on a well-conditioned input; 6 (42
+    bits) do not reach the 1e-14 residual gate and are not offered as an FP64 setting."""
+    n, mode = 520, 1
+    seed, A, o = tie_free_seed(make_input(n, mode, 0), 2600, mode)
+    r = run(A, mode, path=gj.PATH_BLOCKED, update=gj.UPDATE_TC_OZAKI, slices=slices)
     assert_matches_oracle(A, r, o, mode)
 
 
@@ -92,7 +103,8 @@ def test_unblocked_random(n, mode):
     assert_matches_oracle(A, r, o, mode)
 
 
-@pytest.mark.parametrize("path,n", [(gj.PATH_CTA, 40), (gj.PATH_BLOCKED, 150), (gj.PATH_UNBLOCKED, 140)])
+@pytest.mark.parametrize("path,n", [(gj.PATH_CTA, 40), (gj.PATH_BLOCKED, 150), (gj.PATH_BLOCKED, 600),
+                                    (gj.PATH_UNBLOCKED, 140)])
 def test_lda_inplace_and_host_buffers(path, n):
     mode = 1
     _, A, o = tie_free_seed(make_input(n, mode, 0), 4000 + n, mode)
@@ -157,7 +169,7 @@ def test_workload_128_full_pivoting():
 
 def test_workload_8192_partial_blocked():
     """The 8192 x 8192 N(0,1) + 0.1 n I workload in the launch configuration the benchmark
-    times (blocked, partial pivoting, auto panel).  The oracle cannot invert it in test time, so
+    times (blocked, partial pivoting, auto panel and update engine: tensor cores).  The oracle cannot invert it in test time, so
     the checks are properties that hold at any size: column dominance keeps every pivot on
     the diagonal (the oracle shows the same at n = 256 and 512 of this recipe), sampled
     columns and rows satisfy A X = I and X A = I to the normalised-residual gate, the
