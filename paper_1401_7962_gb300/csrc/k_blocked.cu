@@ -21,6 +21,8 @@
 // the pivot and stages the eq. 14 row and the eq. 15 column, a second launch updates
 // the whole array and scans the next step's candidates.
 #include <cooperative_groups.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "gj_ozaki.cuh"
@@ -45,14 +47,66 @@ struct __align__(16) PanelCand {
   double prow[kPanelMaxB];      // eq. 14 row over the panel: row * inv_q, inv_q in the pivot slot
 };
 
+constexpr int kSlots = 3;        // candidate slots: pushes for step t+1 and reads of step t never collide
+constexpr int kRowBlock = 32;    // rows are dealt to the cluster CTAs in blocks of 32, round robin
+constexpr uint64_t kPanelWaitNs = 2000000000ull;
+
 struct PanelSmem {
   static size_t bytes(int cs, int rp, int bb) {
-    size_t s = sizeof(PanelCand) * (size_t)(2 * cs + 1);
-    s += sizeof(double) * (size_t)rp * bb;
-    s += sizeof(int) * (size_t)rp;
+    size_t s = sizeof(PanelCand) * (size_t)(kSlots * cs + 1);
+    s += sizeof(double) * (size_t)(rp + 1) * bb;  // Wp, leading dimension rp + 1
+    s += sizeof(double) * (size_t)rp;             // lrow
+    s += sizeof(int) * (size_t)rp * 2;            // posl, act
     return (s + 15) & ~size_t(15);
   }
 };
+
+// Global row of local row il of cluster CTA `rank` (block-cyclic distribution).
+__device__ __forceinline__ int panel_row(int il, int rank, int cs) {
+  return ((il / kRowBlock) * cs + rank) * kRowBlock + (il % kRowBlock);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+// 16-byte store into another CTA's shared memory, counted in bytes on that CTA's mbarrier.
+__device__ __forceinline__ void st_async16(uint32_t raddr, int4 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(raddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(c) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+  auto once = [&]() {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+  };
+  if (once()) return true;
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    if (once()) return true;
+    uint64_t t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (t1 - t0 > kPanelWaitNs) return false;
+  }
+}
 
 __device__ __forceinline__ void consider3(double v, int key, int il, uint64_t& bv, int& bk, int& bi) {
   const uint64_t a = abs_bits(v);
@@ -77,49 +131,88 @@ __device__ __forceinline__ void warp_argmax3(uint64_t& v, int& key, int& il) {
   }
 }
 
-// Panel of columns [k0, k0+bb) over all n rows, one cluster of `cs` CTAs; CTA r owns
-// rows [r*rp, r*rp + rp).  One cluster barrier per step: after it every CTA holds all
-// candidates of the step (pushed into its shared memory) and picks the same winner.
+// Panel of columns [k0, k0+bb) reduced by one cluster of `cs` CTAs.  Only the rows not yet
+// pivoted when the panel starts ("active" rows: position >= k0) are eliminated step by
+// step -- the pivot search needs nothing else; the rows pivoted earlier end the panel at
+// -N M^-1 (N their panel values at the start, M^-1 the panel's pivot block at the end) and
+// get that from fixup_used_rows_kernel on the whole GPU afterwards.
+//
+// Step t: every CTA waits on its own mbarrier for the candidates of all CTAs, takes the
+// same winner, updates column t+1 of its active rows (eq. 15), finds its candidate for step
+// t+1 and stores it with its eq. 14 row into every CTA's shared memory (st.async, counted
+// on the receiver's mbarrier of that slot), then applies eq. 15 to the other columns.
+// There is no cluster-wide barrier per step: three slots guarantee that a slot is only
+// rewritten after every CTA has finished the step that read it.  Waits are bounded.
 __global__ void __launch_bounds__(kPanelThreads, 1)
     panel_kernel(int n, int k0, int bb, int rp, double* __restrict__ W, int* __restrict__ posrow,
-                 double* __restrict__ Lbuf, int* __restrict__ prow_ids, double* __restrict__ pivots,
-                 int* __restrict__ piv_rows, int32_t* status, int64_t* fail_step, int mode, double tau) {
+                 double* __restrict__ Lbuf, double* __restrict__ Mbuf, int* __restrict__ prow_ids,
+                 double* __restrict__ pivots, int* __restrict__ piv_rows, int32_t* status, int64_t* fail_step,
+                 int mode, double tau) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int cs = (int)cluster.num_blocks();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ldp = rp + 1;
   extern __shared__ __align__(16) char smem[];
-  PanelCand* slots = reinterpret_cast<PanelCand*>(smem);  // [2][cs]
-  PanelCand* stage = slots + 2 * cs;
-  double* Wp = reinterpret_cast<double*>(stage + 1);       // [bb][rp], column-major over own rows
-  int* posl = reinterpret_cast<int*>(Wp + (size_t)rp * bb);
+  PanelCand* slots = reinterpret_cast<PanelCand*>(smem);  // [kSlots][cs]
+  PanelCand* stage = slots + kSlots * cs;
+  double* Wp = reinterpret_cast<double*>(stage + 1);       // [bb][ldp], column-major over own rows
+  double* lrow = Wp + (size_t)ldp * bb;                    // eq. 15 multiplier of the current step
+  int* posl = reinterpret_cast<int*>(lrow + rp);
+  int* act = posl + rp;                                    // local indices of the active rows
+  __shared__ __align__(8) uint64_t slot_bar[kSlots];
   __shared__ uint64_t red_v[kPanelWarps];
-  __shared__ int red_k[kPanelWarps], red_i[kPanelWarps];
+  __shared__ int red_k[kPanelWarps], red_i[kPanelWarps], wcount[kPanelWarps];
+  __shared__ int s_nact;
+  const uint32_t rec_bytes = (uint32_t)(cs * sizeof(PanelCand));
+  // |v| <= tau  <=>  bits(|v|) <= bits(tau) for non-negative binary64 (tau >= 0)
+  const uint64_t tau_bits = static_cast<uint64_t>(__double_as_longlong(tau));
 
   if (*status != GJ_OK) return;  // an earlier step failed (uniform over the cluster)
 
-  const int row0 = rank * rp;
-  const int nrows = max(0, min(rp, n - row0));
-
-  for (int il = tid; il < rp; il += kPanelThreads) posl[il] = (il < nrows) ? posrow[row0 + il] : 0x7fffffff;
+  if (tid == 0) {
+    for (int q = 0; q < kSlots; ++q) bar_init(&slot_bar[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int q = 0; q < kSlots; ++q) bar_expect(&slot_bar[q], rec_bytes);  // phase 0 of every slot
+    s_nact = 0;
+  }
+  for (int il = tid; il < rp; il += kPanelThreads) {
+    const int g = panel_row(il, rank, cs);
+    posl[il] = (g < n) ? posrow[g] : -1;
+  }
   for (int e = tid; e < rp * bb; e += kPanelThreads) {
     const int j = e / rp, il = e - j * rp;
-    Wp[il + j * rp] = (il < nrows) ? W[(int64_t)(row0 + il) + (int64_t)(k0 + j) * n] : 0.0;
+    const int g = panel_row(il, rank, cs);
+    Wp[il + j * ldp] = (g < n) ? W[(int64_t)g + (int64_t)(k0 + j) * n] : 0.0;
   }
-  cluster.sync();  // every CTA of the cluster is running before any remote store
-
-  // Candidate of column t at step k among the own rows; staged and pushed to all CTAs.
-  auto push_candidate = [&](int t, int k, int par) {
-    uint64_t bv = 0;
-    int bk = kNoKey, bi = -1;
-    for (int il = tid; il < nrows; il += kPanelThreads) {
-      const int p = posl[il];
-      if (mode == GJ_PIVOT_NONE) {
-        if (p == k) consider3(Wp[il + t * rp], p, il, bv, bk, bi);
-      } else if (p >= k) {
-        consider3(Wp[il + t * rp], p, il, bv, bk, bi);
-      }
+  __syncthreads();
+  // compact the active rows (order preserved) into act[0 .. s_nact)
+  for (int base = 0; base < rp; base += kPanelThreads) {
+    const int il = base + tid;
+    const bool a = il < rp && posl[il] >= k0;
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) wcount[wid] = __popc(m);
+    __syncthreads();
+    int off = s_nact;
+    for (int w = 0; w < wid; ++w) off += wcount[w];
+    if (a) act[off + __popc(m & ((1u << lane) - 1u))] = il;
+    __syncthreads();
+    if (tid == 0) {
+      int tot = 0;
+      for (int w = 0; w < kPanelWarps; ++w) tot += wcount[w];
+      s_nact += tot;
     }
+    __syncthreads();
+  }
+  const int nact = s_nact;
+  cluster.sync();  // every CTA has armed its slots before any remote store
+
+  // Reduce the per-warp candidates, build the record of the CTA's candidate for step
+  // (k0 + tt) from column tt and store it into every CTA's slot `slot`.  With pend, the
+  // candidate row has a pending eq. 15 update of the previous step (multiplier lrow,
+  // row prow_prev, pivot column tprev) that is applied to its columns on the fly.
+  auto push_candidate = [&](uint64_t bv, int bk, int bi, int tt, int slot, bool pend, const double* prow_prev,
+                            int tprev) {
     warp_argmax3(bv, bk, bi);
     if (lane == 0) {
       red_v[wid] = bv;
@@ -128,57 +221,88 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
     }
     __syncthreads();
     if (wid == 0) {
-      uint64_t v = 0;
-      int key = kNoKey, il = -1;
-      for (int w = 0; w < kPanelWarps; ++w)
-        if (key_better(red_v[w], red_k[w], v, key)) {
-          v = red_v[w];
-          key = red_k[w];
-          il = red_i[w];
-        }
+      uint64_t v = (lane < kPanelWarps) ? red_v[lane] : 0ull;
+      int key = (lane < kPanelWarps) ? red_k[lane] : kNoKey;
+      int il = (lane < kPanelWarps) ? red_i[lane] : -1;
+      warp_argmax3(v, key, il);
       double q = 0.0, inv_q = 0.0;
       if (il >= 0) {
-        q = Wp[il + t * rp];
+        const double l = pend ? lrow[il] : 0.0;
+        q = Wp[il + tt * ldp];  // column tt is already up to date
         if (lane == 0) inv_q = 1.0 / q;
         inv_q = __shfl_sync(0xffffffffu, inv_q, 0);
-        for (int j = lane; j < bb; j += 32) stage->prow[j] = (j == t) ? inv_q : Wp[il + j * rp] * inv_q;
+        for (int j = lane; j < bb; j += 32) {
+          double x = Wp[il + j * ldp];
+          if (pend && j != tt) x = fma(-l, prow_prev[j], (j == tprev) ? 0.0 : x);
+          stage->prow[j] = (j == tt) ? inv_q : x * inv_q;
+        }
       }
       if (lane == 0) {
         stage->absv = v;
         stage->key = key;
-        stage->row = (il >= 0) ? row0 + il : -1;
+        stage->row = (il >= 0) ? panel_row(il, rank, cs) : -1;
         stage->q = q;
         stage->inv_q = inv_q;
       }
     }
     __syncthreads();
-    // warp w copies the staged record into CTA w's slot[par][rank]
-    if (wid < cs) {
-      PanelCand* dst = cluster.map_shared_rank(&slots[par * cs + rank], wid);
+    if (wid < cs) {  // warp w stores the staged record into CTA w's slot
+      const uint32_t dst = map_rank(smem_addr(&slots[slot * cs + rank]), wid);
+      const uint32_t rbar = map_rank(smem_addr(&slot_bar[slot]), wid);
       const int4* src4 = reinterpret_cast<const int4*>(stage);
-      int4* dst4 = reinterpret_cast<int4*>(dst);
       constexpr int kWords = sizeof(PanelCand) / sizeof(int4);
-      for (int w = lane; w < kWords; w += 32) dst4[w] = src4[w];
+      for (int w = lane; w < kWords; w += 32) st_async16(dst + 16u * w, src4[w], rbar);
     }
-    cluster.sync();
   };
 
-  push_candidate(0, k0, 0);
+  {  // step 0 candidates from the panel as loaded
+    uint64_t bv = 0;
+    int bk = kNoKey, bi = -1;
+    for (int a = tid; a < nact; a += kPanelThreads) {
+      const int il = act[a], p = posl[il];
+      if (mode == GJ_PIVOT_NONE ? (p == k0) : (p >= k0)) consider3(Wp[il], p, il, bv, bk, bi);
+    }
+    push_candidate(bv, bk, bi, 0, 0, false, nullptr, 0);
+  }
 
   int failed = 0;
   for (int t = 0; t < bb; ++t) {
     const int k = k0 + t;
-    const int par = t & 1;
-    // every thread takes the same winner from the local copies of all candidates
-    const PanelCand* sl = &slots[par * cs];
+    const int sq = t % kSlots;
+    // all candidates of step t are in slot sq once its phase t / kSlots completes
+    const bool got = bar_wait(&slot_bar[sq], (uint32_t)((t / kSlots) & 1));
+    if (__syncthreads_or(!got)) {
+      if (tid == 0) {
+        atomicExch(status, GJ_ERR_TIMEOUT);
+        *fail_step = k;
+      }
+      failed = 1;
+      break;
+    }
+    if (tid == 0 && t + kSlots < bb) bar_expect(&slot_bar[sq], rec_bytes);  // next use of this slot
+    const PanelCand* sl = &slots[sq * cs];
+    uint64_t av[16];
+    int ak[16];
+#pragma unroll
+    for (int c2 = 0; c2 < 16; ++c2) {  // independent loads first
+      av[c2] = (c2 < cs) ? sl[c2].absv : 0ull;
+      ak[c2] = (c2 < cs) ? sl[c2].key : kNoKey;
+    }
     int ws = 0;
-    for (int c2 = 1; c2 < cs; ++c2)
-      if (key_better(sl[c2].absv, sl[c2].key, sl[ws].absv, sl[ws].key)) ws = c2;
+    uint64_t wv = av[0];
+    int wk = ak[0];
+#pragma unroll
+    for (int c2 = 1; c2 < 16; ++c2)
+      if (key_better(av[c2], ak[c2], wv, wk)) {
+        wv = av[c2];
+        wk = ak[c2];
+        ws = c2;
+      }
     const PanelCand& win = sl[ws];
     int st = GJ_OK;
     if (win.row < 0) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
-    else if (win.absv >= kInfBits) st = GJ_NONFINITE;
-    else if (__longlong_as_double((long long)win.absv) <= tau) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+    else if (wv >= kInfBits) st = GJ_NONFINITE;
+    else if (wv <= tau_bits) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
     if (st != GJ_OK) {
       if (rank == 0 && tid == 0) {
         *status = st;
@@ -187,43 +311,119 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       failed = 1;
       break;
     }
-    const int rpos = win.key, R = win.row;
+    const int rpos = wk, R = win.row;
     if (rank == 0 && tid == 0) {
       pivots[k] = win.q;
       piv_rows[k] = rpos;
       prow_ids[t] = R;
     }
-    // interchange (positions), eq. 14 for the pivot row, eq. 15 for the others
-    for (int il = tid; il < nrows; il += kPanelThreads) {
-      const int grow = row0 + il;
+    const bool next = t + 1 < bb;
+    // part 1: interchange (positions), multipliers, column t+1, next candidates
+    uint64_t bv = 0;
+    int bk = kNoKey, bi = -1;
+    for (int a = tid; a < nact; a += kPanelThreads) {
+      const int il = act[a];
+      const int g = panel_row(il, rank, cs);
       int p = posl[il];
-      if (grow == R) {
+      if (g == R) {
         p = k;
-        for (int j = 0; j < bb; ++j) Wp[il + j * rp] = win.prow[j];
+        lrow[il] = 0.0;
+        if (next) Wp[il + (t + 1) * ldp] = win.prow[t + 1];
       } else {
         if (p == k) p = rpos;
-        const double l = Wp[il + t * rp];
-        for (int j = 0; j < bb; ++j) {
-          const double base = (j == t) ? 0.0 : Wp[il + j * rp];
-          Wp[il + j * rp] = fma(-l, win.prow[j], base);
+        const double l = Wp[il + t * ldp];
+        lrow[il] = l;
+        if (next) {
+          const double nv = fma(-l, win.prow[t + 1], Wp[il + (t + 1) * ldp]);
+          Wp[il + (t + 1) * ldp] = nv;
+          if (mode == GJ_PIVOT_NONE ? (p == k + 1) : (p >= k + 1)) consider3(nv, p, il, bv, bk, bi);
         }
       }
       posl[il] = p;
     }
-    __syncthreads();
-    if (t + 1 < bb) push_candidate(t + 1, k + 1, par ^ 1);
-  }
-
-  if (!failed) {
-    for (int e = tid; e < rp * bb; e += kPanelThreads) {
-      const int j = e / rp, il = e - j * rp;
-      if (il < nrows) {
-        const double v = Wp[il + j * rp];
-        W[(int64_t)(row0 + il) + (int64_t)(k0 + j) * n] = v;
-        Lbuf[(int64_t)(row0 + il) + (int64_t)j * n] = (posl[il] == k0 + j) ? v - 1.0 : v;
+    if (next) push_candidate(bv, bk, bi, t + 1, (t + 1) % kSlots, true, win.prow, t);
+    // part 2: eq. 14 / eq. 15 on the remaining columns while the candidates travel
+    for (int a = tid; a < nact; a += kPanelThreads) {
+      const int il = act[a];
+      const int g = panel_row(il, rank, cs);
+      if (g == R) {
+        for (int j = 0; j < bb; ++j)
+          if (j != t + 1) Wp[il + j * ldp] = win.prow[j];
+      } else {
+        const double l = lrow[il];
+        for (int j = 0; j < bb; ++j) {
+          if (j == t + 1) continue;
+          const double base = (j == t) ? 0.0 : Wp[il + j * ldp];
+          Wp[il + j * ldp] = fma(-l, win.prow[j], base);
+        }
       }
     }
-    for (int il = tid; il < nrows; il += kPanelThreads) posrow[row0 + il] = posl[il];
+  }
+  __syncthreads();
+
+  if (!failed) {
+    for (int e = tid; e < nact * bb; e += kPanelThreads) {
+      const int j = e / nact, a = e - j * nact;
+      const int il = act[a];
+      const int g = panel_row(il, rank, cs);
+      const double v = Wp[il + j * ldp];
+      W[(int64_t)g + (int64_t)(k0 + j) * n] = v;
+      Lbuf[(int64_t)g + (int64_t)j * n] = (posl[il] == k0 + j) ? v - 1.0 : v;
+    }
+    for (int a = tid; a < nact; a += kPanelThreads) {
+      const int il = act[a];
+      const int p = posl[il];
+      posrow[panel_row(il, rank, cs)] = p;
+      if (p >= k0 && p < k0 + bb)  // a pivot row of this panel: its row of M^-1
+        for (int j = 0; j < bb; ++j) Mbuf[(p - k0) * kPanelMaxB + j] = Wp[il + j * ldp];
+    }
+  }
+  cluster.sync();  // no CTA leaves while stores into its shared memory may be in flight
+}
+
+// Rows pivoted before the panel (position < k0): W[i, P] <- -W[i, P] M^-1 with
+// M^-1[s, t] = Mbuf[s * 64 + t] (the panel's pivot block, written by the panel); L gets the
+// same values (these rows are not pivot rows of the panel).  A warp takes 32 consecutive
+// rows and one column t, so loads and stores are coalesced and M^-1[., t] is a broadcast.
+__global__ void __launch_bounds__(256) fixup_used_rows_kernel(int n, int k0, int bb, double* __restrict__ W,
+                                                              const int* __restrict__ posrow,
+                                                              const double* __restrict__ Mbuf,
+                                                              double* __restrict__ Lbuf, const int32_t* status) {
+  if (*status != GJ_OK || k0 == 0) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const bool used = i < n && posrow[i] < k0;
+  if (!__syncthreads_or(used)) return;  // uniform over the block (same 32 rows in every warp)
+  __shared__ double Minv[kPanelMaxB][kPanelMaxB];
+  for (int e = threadIdx.x; e < bb * kPanelMaxB; e += blockDim.x) Minv[e / kPanelMaxB][e % kPanelMaxB] = Mbuf[e];
+  __syncthreads();
+  double o[kPanelMaxB];
+#pragma unroll
+  for (int s2 = 0; s2 < kPanelMaxB; ++s2)
+    o[s2] = (used && s2 < bb) ? W[(int64_t)i + (int64_t)(k0 + s2) * n] : 0.0;
+  double acc[kPanelMaxB / 8];
+#pragma unroll
+  for (int c = 0; c < kPanelMaxB / 8; ++c) acc[c] = 0.0;
+  // warp w of 8 handles columns t = w, w + 8, ...
+#pragma unroll
+  for (int s2 = 0; s2 < kPanelMaxB; ++s2) {
+    if (s2 >= bb) break;
+#pragma unroll
+    for (int c = 0; c < kPanelMaxB / 8; ++c) {
+      const int t2 = w + 8 * c;
+      if (t2 < bb) acc[c] = fma(o[s2], Minv[s2][t2], acc[c]);
+    }
+  }
+  __syncwarp();
+  __syncthreads();  // every old value read before any column is overwritten
+  if (!used) return;
+#pragma unroll
+  for (int c = 0; c < kPanelMaxB / 8; ++c) {
+    const int t2 = w + 8 * c;
+    if (t2 < bb) {
+      W[(int64_t)i + (int64_t)(k0 + t2) * n] = -acc[c];
+      Lbuf[(int64_t)i + (int64_t)t2 * n] = -acc[c];
+    }
   }
 }
 
@@ -609,6 +809,7 @@ struct WsList {
 
 // Choose the cluster size and panel width for order n; returns the shared memory bytes.
 static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* rp_out) {
+  // rp: rows per CTA, whole 32-row blocks dealt round robin
   int cs = (int)((n + 255) / 256);
   if (cs < 1) cs = 1;
   if (cs > 16) cs = 16;
@@ -616,7 +817,8 @@ static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* 
   int b = want_b > 0 ? want_b : 32;
   if (b > kPanelMaxB) b = kPanelMaxB;
   for (;;) {
-    const int rp = (int)((n + cs - 1) / cs);
+    const int64_t blocks = (n + kRowBlock - 1) / kRowBlock;
+    const int rp = (int)((blocks + cs - 1) / cs) * kRowBlock;
     const size_t bytes = PanelSmem::bytes(cs, rp, b);
     if (bytes <= limit || b <= 4) {
       *cs_out = cs;
@@ -652,6 +854,8 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   GJ_WS(posrow, (size_t)n);
   GJ_WS(rowat, (size_t)n);
   GJ_WS(prow_ids, (size_t)Bw);
+  double* Mbuf;
+  GJ_WS(Mbuf, (size_t)kPanelMaxB * kPanelMaxB);
   GJ_WS(oz_err, 4);
   if (tc) {
     uint8_t* p8;
@@ -710,12 +914,25 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
       const int bb = (K0 + BB - k0 < b) ? K0 + BB - k0 : b;
       {
         ProfScope ps(s, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
-        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, prow_ids + (k0 - K0), pivots,
-                                   piv_rows, out.status, out.fail_step, pivot_mode, tau));
+        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, Mbuf, prow_ids + (k0 - K0),
+                                   pivots, piv_rows, out.status, out.fail_step, pivot_mode, tau));
       }
       prof_count(1);
+      if (k0 > 0) {
+        ProfScope ps(s, "fixup_used_rows", 2.0 * k0 * (double)bb * bb, 16.0 * k0 * (double)bb);
+        fixup_used_rows_kernel<<<(n + 31) / 32, 256, 0, s>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
+        GJ_CUDA(cudaGetLastError());
+        prof_count(1);
+      }
       if (BB > bb) {  // the rest of the outer panel
-        gj_status st = fp64_update(k0, bb, K0, K0 + BB, prow_ids + (k0 - K0));
+        gj_status st;
+        if (tc) {
+          // columns [K0, K0 + BB) of W; U = the sub-panel's pivot rows, zero on the sub-panel
+          st = ozaki_update(n, BB, bb, Lbuf, n, nullptr, W + (size_t)K0 * n, n, prow_ids + (k0 - K0), k0 - K0,
+                            k0 - K0 + bb, W + (size_t)K0 * n, n, S, oz_ws, oz_err, out.status, s);
+        } else {
+          st = fp64_update(k0, bb, K0, K0 + BB, prow_ids + (k0 - K0));
+        }
         if (st != GJ_OK) return st;
       }
     }
