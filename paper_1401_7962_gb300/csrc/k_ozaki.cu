@@ -165,6 +165,35 @@ __global__ void slice_cols_kernel(int N, int K, const double* __restrict__ U, in
 
 // ---------------------------------------------------------------- tensor-core update
 
+// T * 2^e rounded to nearest (even) in binary64, built with integer operations only
+// (the FP64 pipe of GB300 is narrow; this keeps the conversion off it).
+__device__ __forceinline__ double i64_times_pow2(long long T, int e) {
+  const unsigned long long sgn = (T < 0) ? 0x8000000000000000ull : 0ull;
+  unsigned long long a = (T < 0) ? (0ull - static_cast<unsigned long long>(T)) : static_cast<unsigned long long>(T);
+  int msb = 63 - __clzll(static_cast<long long>(a));
+  unsigned long long m;
+  if (msb <= 52) {
+    m = a << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    m = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      ++msb;
+    }
+  }
+  const int biased = msb + e + 1023;
+  if (biased <= 0 || biased >= 2047) return ldexp(static_cast<double>(T), e);  // outside the normal range
+  return __longlong_as_double(static_cast<long long>(sgn | (static_cast<unsigned long long>(biased) << 52) |
+                                                     (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// Arrive for a barrier of a digit group that does not exist at this slice count (keeps the
+// per-group barrier phases of all eight groups in step).
+__device__ __forceinline__ void mbar_arrive_unused(uint64_t* bar) { tc::mbar_arrive(bar); }
+
 struct SmemLayout {
   static size_t bytes(int S) {
     return 1024 /*align slack*/ + (size_t)S * 2 * kBBox + (size_t)kStages * kABox + (size_t)2 * kCSm * kTM * 8;
@@ -194,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* Aring = smem + (size_t)S * 2 * kBBox;          // [kStages] boxes of 16 KiB
   double* Cs = reinterpret_cast<double*>(Aring + (size_t)kStages * kABox);  // [2 halves][kCSm][kTM]
   __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_full[kStages], bar_empty[kStages], bar_accfull,
-      bar_accempty, bar_fin;
+      bar_gfree[8], bar_fin;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
 
@@ -207,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&bar_empty[i], 1);
     }
     tc::mbar_init(&bar_accfull, 1);
-    tc::mbar_init(&bar_accempty, kEpiThreads);
+    for (int g = 0; g < 8; ++g) tc::mbar_init(&bar_gfree[g], kEpiThreads);
     tc::mbar_init(&bar_fin, 1);
     tc::fence_mbar_init();
     s_abort = 0;
@@ -239,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int idx = blockIdx.x; idx < ntiles && !s_abort; idx += gridDim.x, ++local) {
         int m0, c0;
         tile_of(idx, m0, c0);
-        if (local > 0 && !tc::mbar_wait(&bar_bempty, (uint32_t)((local - 1) & 1), kWaitNs)) {
+        if (local > 0 && !tc::mbar_wait_backoff(&bar_bempty, (uint32_t)((local - 1) & 1), kWaitNs)) {
           atomicExch(err, 10);
           s_abort = 1;
           break;
@@ -253,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int sl = 0; sl < S && ok; ++sl)
           for (int kc = 0; kc < nkc; ++kc, ++it) {
             const int stage = it % kStages, use = it / kStages;
-            if (use > 0 && !tc::mbar_wait(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
+            if (use > 0 && !tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
               atomicExch(err, 11);
               s_abort = 1;
               ok = false;
@@ -272,7 +301,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0, local = 0;
       for (int idx = blockIdx.x; idx < ntiles && !s_abort; idx += gridDim.x, ++local) {
         bool ok = tc::mbar_wait(&bar_bfull, (uint32_t)(local & 1), kWaitNs);
-        if (ok && local > 0) ok = tc::mbar_wait(&bar_accempty, (uint32_t)((local - 1) & 1), kWaitNs);
         if (!ok) {
           atomicExch(err, 20);
           s_abort = 1;
@@ -289,12 +317,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::tc_fence_after();
             const uint64_t a0 = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kABox));
             for (int t = 0; sl + t < S; ++t) {
+              if (sl == 0 && kc == 0 && local > 0) {
+                // first write of group t in this tile: the epilogue must have drained it
+                if (!tc::mbar_wait(&bar_gfree[t], (uint32_t)((local - 1) & 1), kWaitNs)) {
+                  ok = false;
+                  break;
+                }
+                tc::tc_fence_after();
+              }
               const uint32_t d = tmem + (uint32_t)(kTN * (sl + t));
               const uint64_t b0 = tc::desc_k128_sw128(tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox));
 #pragma unroll
               for (int k16 = 0; k16 < kKC / 16; ++k16)
                 tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
             }
+            if (!ok) break;
             tc::mma_commit(&bar_empty[stage]);
           }
         }
@@ -337,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         cv[c] = (row_ok && gj < N) ? C[(int64_t)gi + (int64_t)gj * ldc] : 0.0;
       }
       const int er = row_ok ? erow[gi] : 0;
-      bool ok = tc::mbar_wait(&bar_accfull, (uint32_t)(local & 1), kWaitNs);
+      bool ok = tc::mbar_wait_backoff(&bar_accfull, (uint32_t)(local & 1), kWaitNs);
       ok = __all_sync(0xffffffffu, ok) && !__any_sync(0xffffffffu, s_abort != 0);
       if (!ok) {
         atomicExch(err, 30);
@@ -345,46 +382,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc::tc_fence_after();
-      tc::cp_async_wait_all();
+      // drain the groups in order, releasing each to the next tile's MMAs as soon as it is read
+      long long T[kEpiCols];
 #pragma unroll
-      for (int cc = 0; cc < kEpiCols / 8; ++cc) {
-        // all groups of this 8-column chunk in flight before one wait
-        uint32_t v[8][8];
+      for (int c = 0; c < kEpiCols; ++c) T[c] = 0;
+      for (int g = 0; g < S; ++g) {
+        uint32_t v[kEpiCols / 8][8];
 #pragma unroll
-        for (int g = 0; g < 8; ++g)
-          if (g < S) tc::tmem_ld8(lane_base + (uint32_t)(kTN * g + 8 * cc), v[g]);
+        for (int cc = 0; cc < kEpiCols / 8; ++cc) tc::tmem_ld8(lane_base + (uint32_t)(kTN * g + 8 * cc), v[cc]);
         tc::tmem_ld_wait();
-        long long T[8];
+        tc::tc_fence_before();
+        tc::mbar_arrive(&bar_gfree[g]);
+        const int sh = 55 - 7 * (g + 2);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) T[c] = 0;
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          if (g >= S) continue;
-          const int sh = 55 - 7 * (g + 2);
+        for (int cc = 0; cc < kEpiCols / 8; ++cc)
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            const long long G = static_cast<long long>(__float2int_rn(__uint_as_float(v[g][c])));
-            T[c] += (sh >= 0) ? (G << sh) : (G >> (-sh));
+            const long long G = static_cast<long long>(__float2int_rn(__uint_as_float(v[cc][c])));
+            T[8 * cc + c] += (sh >= 0) ? (G << sh) : (G >> (-sh));
           }
-        }
-        if (row_ok) {
+      }
+      for (int g = S; g < 8; ++g) mbar_arrive_unused(&bar_gfree[g]);
+      tc::cp_async_wait_all();
+      if (row_ok) {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int cl = 8 * cc + c;
-            const int gj = c0 + cl;
-            if (gj >= N || (gj >= skip_lo && gj < skip_hi) || T[c] == 0) continue;
-            const int e = er + ecol[gj] - 55;
-            const double d = __ll2double_rn(T[c]);
-            const double cold = (cl < kCSm) ? Csh[cl * kTM + r] : cv[cl - kCSm];
-            const double out = (e >= -1022 && e <= 1023)
-                                   ? fma(d, __longlong_as_double(static_cast<long long>(e + 1023) << 52), cold)
-                                   : cold + ldexp(d, e);
-            C[(int64_t)gi + (int64_t)gj * ldc] = out;
-          }
+        for (int cl = 0; cl < kEpiCols; ++cl) {
+          const int gj = c0 + cl;
+          if (gj >= N || (gj >= skip_lo && gj < skip_hi) || T[cl] == 0) continue;
+          const double cold = (cl < kCSm) ? Csh[cl * kTM + r] : cv[cl - kCSm];
+          C[(int64_t)gi + (int64_t)gj * ldc] = cold + i64_times_pow2(T[cl], er + ecol[gj] - 55);
         }
       }
-      tc::tc_fence_before();
-      tc::mbar_arrive(&bar_accempty);
     }
   }
 
