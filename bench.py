@@ -55,6 +55,8 @@ WORKLOADS = {
     "inv128": dict(n=128, shift=0.0, pivot=2, seed=wl.SEED_BASE + 1, name="gj-inverse-128-fp64-full-cta"),
     "batch200k": dict(count=200_000, seed=wl.SEED_BASE + 3, pivot=1,
                       name="gj-batched-200k-n4to64-fp64-partial"),
+    "mixed16384": dict(n=16384, kappa=1e6, pivot=1, seed=wl.SEED_BASE + 4,
+                       name="gj-inverse-16384-fp32in-mixed-refined"),
 }
 
 
@@ -202,6 +204,14 @@ def cpu_oracle_sample(workload: str, repeat: int = 1) -> dict:
         return {"value": take / dt, "unit": "matrices/s", "cores": cores, "kind": "oracle",
                 "sample": f"first {take} of the 200000 matrices, oracle over {cores} threads",
                 "gflops": float((2.0 * sizes.astype(np.float64) ** 3).sum() / dt / 1e9)}
+    if workload == "mixed16384":
+        n = 1536
+        A = wl.svd_conditioned(n, W["kappa"], W["seed"], dtype=np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.invert(A, W["pivot"])
+        dt = time.perf_counter() - t0
+        return {"value": 2.0 * n ** 3 / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                "sample": f"FP64 oracle on one {n}x{n} matrix of the same recipe (kappa 1e6), 1 thread"}
     n = 2048 if workload == "inv8192" else W["n"]
     A = wl.gaussian(n, W["seed"], shift=W["shift"] * n)
     reps = repeat if workload == "inv8192" else max(repeat, 50)
@@ -293,6 +303,24 @@ def run_gpu(args) -> None:
         per_launch_flops = flops_step
         h2d = packed.nbytes + 8 * count * 2 + 4 * count
         d2h = packed.nbytes + count * (4 + 1 + 8)
+    elif args.workload == "mixed16384":
+        n = W["n"]
+        dA32 = wl.svd_conditioned_device(n, W["kappa"], W["seed"] + rank, device=dev)
+        dX = torch.empty((n, n), dtype=torch.float64, device=dev).t().contiguous().t()
+        flops_step = 2.0 * n ** 3
+        units_step = 1
+        mixed_state = {}
+
+        def step():
+            r = gj.invert_mixed(dA32, out=dX, x0_slices=args.x0_slices, corr_slices=4, tol=1e-12, max_iter=10,
+                                stream=stream)
+            if r["status"] != 0:
+                raise RuntimeError(f"gj_invert_mixed: {gj.status_string(r['status'])}")
+            mixed_state.update(r)
+
+        dominant = "update_ozaki_tc"
+        h2d = 4 * n * n
+        d2h = 8 * n * n
     else:
         n = W["n"]
         A = wl.gaussian(n, W["seed"] + rank, shift=W["shift"] * n)
@@ -389,6 +417,26 @@ def run_gpu(args) -> None:
         roof["avg_launch_ms"] = round(avg_ms, 6)
         roof["share_of_step"] = round(d["total_ms"] / ms, 4)
 
+    if args.workload == "mixed16384":
+        n = W["n"]
+        extra["resid"] = mixed_state.get("resid")
+        extra["refinement_steps"] = mixed_state.get("iters")
+        extra["x0_rung_slices"] = [args.x0_slices, max(args.x0_slices, 5), 8][mixed_state.get("rung", 0)]
+        # the plain FP64-level Gauss-Jordan on the same matrix (converted exactly to FP64)
+        dA64 = dA32.double().t().contiguous().t()
+        for eng, label in ((gj.UPDATE_TC_OZAKI, "fp64_gj_tensor_update"), (gj.UPDATE_DFMA, "fp64_gj_fma_update")):
+            if eng == gj.UPDATE_DFMA and not args.compare_fma:
+                continue
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            rr = gj.invert(dA64, gj.PIVOT_PARTIAL, out=dX, update=eng, stream=stream)
+            c1.record(stream)
+            c1.synchronize()
+            extra[label + "_ms"] = c0.elapsed_time(c1)
+            extra[label + "_gflops"] = 2.0 * n ** 3 / (c0.elapsed_time(c1) / 1000.0) / 1e9
+        del dA64
+
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if (rank == 0 or world > 1) and not args.no_e2e:
@@ -415,6 +463,11 @@ def run_gpu(args) -> None:
                 f"tensor cores: bf16 digit slices (S={args.slices or 8}), exact fp32 group sums, int64 recombination"
             cfg.update({"n": W["n"], "update": args.update, "update_engine": eng,
                         "input": "N(0,1) + 0.1 n I, seed 1403"})
+        elif args.workload == "mixed16384":
+            cfg.update({"n": W["n"], "kappa": W["kappa"], "tol": 1e-12,
+                        "input": "U diag(sigma) V^T, Haar U,V, sigma log-spaced 1..1e6, FP32, seed 1405 (GPU QR)",
+                        "method": "reduced-precision blocked GJ (tensor update, x0 slices) + Newton-Schulz, "
+                                  "FP64-level residual"})
         elif args.workload == "inv128":
             cfg.update({"n": W["n"], "input": "N(0,1), seed 1402"})
         else:
@@ -446,8 +499,22 @@ def run_e2e(args, gj, L, W, stream, dev, h2d, d2h, units_step, flops_step, rank)
     the inputs host -> device and the results device -> host inside the timed region."""
     import ctypes
     import torch
-    steps = max(1, min(args.steps, 3)) if args.workload == "inv8192" else args.steps
-    if args.workload == "batch200k":
+    steps = max(1, min(args.steps, 3)) if args.workload in ("inv8192", "mixed16384") else args.steps
+    if args.workload == "mixed16384":
+        n = W["n"]
+        hA = wl.svd_conditioned_device(n, W["kappa"], W["seed"] + rank, device=dev).cpu().pin_memory()
+        hA = hA.t().contiguous().t() if hA.stride(0) != 1 else hA
+        hX = torch.empty((n, n), dtype=torch.float64).t().contiguous().t().pin_memory()
+        dA = torch.empty((n, n), dtype=torch.float32, device=dev).t().contiguous().t()
+        dX = torch.empty((n, n), dtype=torch.float64, device=dev).t().contiguous().t()
+
+        def one():
+            with torch.cuda.stream(stream):
+                dA.copy_(hA, non_blocking=True)
+                gj.invert_mixed(dA, out=dX, x0_slices=args.x0_slices, corr_slices=4, tol=1e-12, stream=stream)
+                hX.copy_(dX, non_blocking=True)
+            stream.synchronize()
+    elif args.workload == "batch200k":
         sizes, packed, offsets = wl.diag_dominant_batch(W["count"], W["seed"] + rank)
         count = len(sizes)
         hA = torch.from_numpy(packed).pin_memory()
@@ -476,6 +543,24 @@ def run_e2e(args, gj, L, W, stream, dev, h2d, d2h, units_step, flops_step, rank)
                 h_sg.copy_(sg, non_blocking=True)
                 h_lg.copy_(lg, non_blocking=True)
             stream.synchronize()
+    elif args.workload == "mixed16384":
+        n = W["n"]
+        dA32 = wl.svd_conditioned_device(n, W["kappa"], W["seed"] + rank, device=dev)
+        dX = torch.empty((n, n), dtype=torch.float64, device=dev).t().contiguous().t()
+        flops_step = 2.0 * n ** 3
+        units_step = 1
+        mixed_state = {}
+
+        def step():
+            r = gj.invert_mixed(dA32, out=dX, x0_slices=args.x0_slices, corr_slices=4, tol=1e-12, max_iter=10,
+                                stream=stream)
+            if r["status"] != 0:
+                raise RuntimeError(f"gj_invert_mixed: {gj.status_string(r['status'])}")
+            mixed_state.update(r)
+
+        dominant = "update_ozaki_tc"
+        h2d = 4 * n * n
+        d2h = 8 * n * n
     else:
         n = W["n"]
         A = wl.gaussian(n, W["seed"] + rank, shift=W["shift"] * n)
@@ -517,6 +602,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="inv8192")
     ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
     ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 8)")
+    ap.add_argument("--x0-slices", type=int, default=3, help="digit slices of the mixed path's first inverse")
+    ap.add_argument("--compare-fma", action="store_true", help="mixed workload: also time the FP64-FMA update GJ")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -172,6 +172,30 @@ gj_status gj_invert_batched_noalloc(int64_t count, int32_t nmax, const int32_t* 
 gj_status gj_gemm_update_emulated(int64_t M, int64_t N, int64_t K, const double* L, int64_t ldl, const double* U,
                                   int64_t ldu, double* C, int64_t ldc, int slices, void* stream);
 
+/*
+ * gj_invert_mixed -- inverse of an FP32 matrix by reduced-precision Gauss-Jordan plus
+ * Newton-Schulz refinement (not in the paper; an accelerated variant of eqs. 14-15).
+ *   X0: blocked Gauss-Jordan (partial pivoting) whose rank-128 updates run on the BF16
+ *       tensor cores with x0_slices 7-bit digit slices per operand (1: ~8 bits, 2: ~15,
+ *       3: ~22 bits of each row / column scale); pivot search, division and log2|det|
+ *       stay FP64.
+ *   refinement: R = I - A X formed to FP64 level (exact 128-wide chunks of the emulated
+ *       update), X <- X + X R with corr_slices slices, until
+ *       ||A X - I||_F / (||A||_F ||X||_F) <= tol.  A rung that does not contract is
+ *       replaced by the next (x0_slices -> max(x0_slices, 5) -> 8).
+ *   n, A, lda   FP32 column-major input, device memory, lda >= max(1, n).
+ *   X           [n * n] FP64 output, device memory, leading dimension n.
+ *   x0_slices, corr_slices   1..8.   tol > 0.   max_iter >= 0 refinement steps per rung.
+ *   resid_out, iters_out, rung_out   host outputs (may be NULL): final normalised residual,
+ *               refinement steps of the last rung, index of that rung (0..2).
+ *   det_sign, det_log2   host outputs (may be NULL): from the pivots of the last X0.
+ * Returns GJ_NOT_CONVERGED when no rung reaches tol (X holds the last iterate).
+ * Synchronous.  Workspace: about 4 n^2 doubles plus the blocked path's.
+ */
+gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, double* X, int x0_slices, int corr_slices,
+                          double tol, int max_iter, double* resid_out, int* iters_out, int* rung_out, int* det_sign,
+                          double* det_log2, void* stream);
+
 /* A batched plan fixes the orders (host copy given at creation), precomputes the
  * largest-first work order and launch shape, and can be replayed as a CUDA graph. */
 typedef struct gj_plan gj_plan;

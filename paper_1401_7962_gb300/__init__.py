@@ -16,7 +16,7 @@ import os
 
 from . import _build
 
-__all__ = ["lib", "invert", "invert_batched", "invert_batched_noalloc", "BatchedPlan", "GJError", "colmajor", "status_string",
+__all__ = ["lib", "invert", "invert_mixed", "invert_batched", "invert_batched_noalloc", "BatchedPlan", "GJError", "colmajor", "status_string",
            "PIVOT_NONE", "PIVOT_PARTIAL", "PIVOT_FULL"]
 
 OK, SINGULAR, ZERO_PIVOT, NONFINITE, NOT_CONVERGED = 0, 1, 2, 3, 4
@@ -62,6 +62,8 @@ def lib() -> ctypes.CDLL:
     L.gj_invert_batched_noalloc.argtypes = [I64, I32, P, P, P, I, P, P, P, P]
     L.gj_gemm_update_emulated.restype = I
     L.gj_gemm_update_emulated.argtypes = [I64, I64, I64, P, I64, P, I64, P, I64, I, P]
+    L.gj_invert_mixed.restype = I
+    L.gj_invert_mixed.argtypes = [I64, P, I64, P, I, I, D, I, P, P, P, P, P, P]
     L.gj_batched_plan_create.restype = I
     L.gj_batched_plan_create.argtypes = [ctypes.POINTER(P), I64, P, I]
     L.gj_batched_plan_execute.restype = I
@@ -191,6 +193,31 @@ def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, pa
         for k in ("piv_rows", "piv_cols", "pivots"):
             res[k] = rec[k][:n].copy()
     return res
+
+
+def invert_mixed(A32, out=None, *, x0_slices: int = 3, corr_slices: int = 4, tol: float = 1e-12,
+                 max_iter: int = 10, stream=None) -> dict:
+    """``gj_invert_mixed``: FP32 device matrix (column-major) -> FP64 inverse by reduced-precision
+    Gauss-Jordan plus Newton-Schulz refinement.  Returns a dict with ``X``, ``status``,
+    ``resid``, ``iters``, ``rung``, ``det_sign``, ``det_log2``."""
+    L = lib()
+    if A32.ndim != 2 or A32.shape[0] != A32.shape[1] or str(A32.dtype) != "torch.float32":
+        raise ValueError("square float32 torch tensor expected")
+    n = int(A32.shape[0])
+    s0, s1 = A32.stride()
+    if n > 1 and (s0 != 1 or s1 < n):
+        raise ValueError("matrix must be column-major")
+    import torch
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float64, device=A32.device).t().contiguous().t()
+    r, it, rg, sg, lg = ctypes.c_double(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+    st = L.gj_invert_mixed(n, _ptr(A32), max(1, int(s1) if n > 1 else 1), _ptr(out), int(x0_slices), int(corr_slices),
+                           float(tol), int(max_iter), ctypes.addressof(r), ctypes.addressof(it), ctypes.addressof(rg),
+                           ctypes.addressof(sg), ctypes.addressof(lg), _stream_handle(stream))
+    if st < 0:
+        raise GJError(st, "gj_invert_mixed")
+    return {"X": out, "status": st, "resid": r.value, "iters": it.value, "rung": rg.value, "det_sign": sg.value,
+            "det_log2": lg.value}
 
 
 def invert_batched(n_dev, A_ptrs, X_ptrs, status, det_sign=None, det_log2=None, *, pivot_mode: int = PIVOT_PARTIAL,

@@ -95,3 +95,25 @@ def svd_conditioned(n: int, kappa: float, seed: int, dtype=np.float32) -> np.nda
     sigma = np.logspace(0.0, np.log10(kappa), n) if n > 1 else np.ones(n)
     A = (U * sigma[None, :]) @ V.T
     return np.asfortranarray(A.astype(dtype))
+
+
+def svd_conditioned_device(n: int, kappa: float, seed: int, device="cuda"):
+    """U diag(sigma) V^T on the GPU in FP32 (torch): U, V Haar (QR of a seeded N(0,1) matrix,
+    columns sign-fixed by diag(R)), sigma log-spaced from 1 to kappa.  Column-major
+    (Fortran-ordered) FP32 tensor.  For sizes where a host QR would take minutes."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+
+    def haar():
+        Z = torch.randn((n, n), generator=g, device=device, dtype=torch.float32)
+        Q, R = torch.linalg.qr(Z)
+        d = torch.sign(torch.diagonal(R))
+        d[d == 0] = 1.0
+        return Q * d[None, :]
+
+    U = haar()
+    V = haar()
+    sigma = torch.logspace(0.0, float(np.log10(kappa)), n, device=device, dtype=torch.float32)
+    A = (U * sigma[None, :]) @ V.T
+    return A.t().contiguous().t()

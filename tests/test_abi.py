@@ -77,6 +77,11 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.gj_invert_batched(3, 0, p, p, p, 9, p, None, None, None) == gj.ERR_ARG
     assert L.gj_invert_batched(3, 129, p, p, p, 1, p, None, None, None) == gj.ERR_UNSUPPORTED
     assert L.gj_invert_batched(0, 0, None, None, None, 1, None, None, None, None) == gj.OK
+    # mixed: bad slices / tol / lda
+    assert L.gj_invert_mixed(4, p, 4, p, 0, 4, 1e-12, 5, None, None, None, None, None, None) == gj.ERR_ARG
+    assert L.gj_invert_mixed(4, p, 4, p, 3, 4, 0.0, 5, None, None, None, None, None, None) == gj.ERR_ARG
+    assert L.gj_invert_mixed(4, p, 3, p, 3, 4, 1e-12, 5, None, None, None, None, None, None) == gj.ERR_ARG
+    assert L.gj_invert_mixed(0, None, 1, None, 3, 4, 1e-12, 5, None, None, None, None, None, None) == gj.OK
     plan = ctypes.c_void_p()
     nh = np.array([4, 200], dtype=np.int32)
     assert L.gj_batched_plan_create(ctypes.byref(plan), 2, nh.ctypes.data, 1) == gj.ERR_UNSUPPORTED

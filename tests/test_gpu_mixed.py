@@ -1,0 +1,65 @@
+"""Reduced-precision Gauss-Jordan + Newton-Schulz refinement (gj_invert_mixed) against the
+FP64 oracle, on A = U diag(sigma) V^T with Haar U, V and log-spaced sigma, stored as FP32.
+
+What is checked: the normalised residual ||A X - I||_F / (||A||_F ||X||_F) reaches the
+requested tolerance (1e-12); the refined X agrees with the oracle's inverse of the same
+FP32 matrix (converted exactly to FP64) to the forward-error level of a backward-stable
+inverse, 64 n kappa eps relative in the Frobenius norm; the determinant sign equals the
+oracle's and log2|det| (from the reduced-precision pivots) is within the error that the
+X0 precision allows, n kappa 2^-(7 S) relative."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1401_7962_gb300 as gj
+from paper_1401_7962_gb300 import workloads as wl
+from tests.parity import norm_resid
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+EPS = float(np.finfo(np.float64).eps)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1401_7962_gb300 import _build
+    _build.build()
+    gj.lib()
+
+
+@pytest.mark.parametrize("n,kappa,x0", [(300, 1e2, 1), (520, 1e4, 2), (700, 1e6, 5), (1000, 1e6, 3)])
+def test_mixed_refined_inverse(n, kappa, x0):
+    A32 = wl.svd_conditioned(n, kappa, seed=5000 + n, dtype=np.float32)
+    A = A32.astype(np.float64)
+    o = oracle.invert(A, oracle.PIVOT_PARTIAL)
+    dA = torch.from_numpy(np.asfortranarray(A32)).cuda()
+    r = gj.invert_mixed(dA, x0_slices=x0, corr_slices=4, tol=1e-12, max_iter=10)
+    X = r["X"].cpu().numpy()
+    assert r["status"] == 0, r
+    assert r["resid"] <= 1e-12
+    # independent recomputation of the gate on the host
+    R = A @ X - np.eye(n)
+    assert np.linalg.norm(R) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 2e-12
+    kap = np.linalg.cond(A, 2)
+    rel = np.linalg.norm(X - o["X"]) / np.linalg.norm(o["X"])
+    assert rel <= 64 * n * kap * EPS, (rel, kap)
+    assert r["det_sign"] == o["det_sign"]
+    S_used = [x0, max(x0, 5), 8][r["rung"]]
+    assert abs(r["det_log2"] - o["det_log2"]) <= max(1e-9, n * kap * 2.0 ** (-7 * S_used)) * max(1.0, abs(o["det_log2"]))
+
+
+def test_mixed_ladder_climbs_when_x0_too_coarse():
+    """kappa = 1e6 with 1-slice X0 cannot contract (2^-7 kappa >> 1): the ladder moves up."""
+    n = 400
+    A32 = wl.svd_conditioned(n, 1e6, seed=77, dtype=np.float32)
+    r = gj.invert_mixed(torch.from_numpy(np.asfortranarray(A32)).cuda(), x0_slices=1, tol=1e-12)
+    assert r["status"] == 0 and r["rung"] >= 1
+
+
+def test_mixed_reports_nonconvergence():
+    n = 200
+    A32 = wl.svd_conditioned(n, 1e2, seed=78, dtype=np.float32)
+    r = gj.invert_mixed(torch.from_numpy(np.asfortranarray(A32)).cuda(), x0_slices=3, tol=1e-30, max_iter=3)
+    assert r["status"] == gj.NOT_CONVERGED and r["resid"] < 1e-13
