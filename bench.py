@@ -45,8 +45,9 @@ FP64_NOMINAL_GFLOPS = 1250.0
 # benchmark's order by the n^2 elements one update launch touches.  Set an entry to None
 # when its kernel changes, until it is captured again.
 NCU_TRAFFIC = {
-    "update_dfma": {"n": 6144, "bytes": 305.597184e6 + 240.446464e6},
-    "update_ozaki_tc": None,
+    "update_dfma": None,  # column-window change since profiles/update_dfma_inv6144.md
+    "update_ozaki_tc": {"n": 6144, "bytes": 323.975936e6 + 257.463296e6},
+    "cta_batched": {"count": 20000, "bytes": 237.430528e6 + 190.470656e6},
 }
 
 WORKLOADS = {
@@ -410,8 +411,10 @@ def run_gpu(args) -> None:
         achieved_gflops = fl / (avg_ms / 1000.0) / 1e9
         traffic = args.traffic
         t = NCU_TRAFFIC.get(dominant)
-        if traffic is None and t and "n" in W:
+        if traffic is None and t and "n" in W and "n" in t:
             traffic = t["bytes"] * (W["n"] / t["n"]) ** 2
+        if traffic is None and t and "count" in W and "count" in t:
+            traffic = t["bytes"] * W["count"] / t["count"]
         roof = roofline_fp64(achieved_gflops, traffic)
         roof["kernel"] = dominant
         roof["avg_launch_ms"] = round(avg_ms, 6)
