@@ -17,12 +17,12 @@
 // The truncation error per entry is below 2^-7S relative to the row / column scale (S = 7:
 // 2^-49; S = 8: 2^-56), i.e. at the level of an FP64 product's rounding.
 //
-// Kernel shape: one CTA per 128 x 64 tile of C, 4 warps.  Warp 0 issues the TMA loads
-// (all S digit slices of the U tile stay resident; the L slices stream through a
-// 4-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), and all
-// four warps run the epilogue (thread = row of the tile, TMEM lane = row).  Every mbarrier
-// wait is bounded in time; on expiry the kernel records an error, drains its own TMA
-// loads and MMAs, frees its tensor memory and returns.
+// Kernel shape: persistent, one CTA per SM walking 128 x 64 tiles of C.  Warp 0 issues the
+// TMA loads (all S digit slices of the U tile stay resident; the L slices stream through a
+// 4-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), eight
+// warps run the epilogue (TMEM lane = row of the tile).  Every mbarrier wait is bounded in
+// time; on expiry the kernel records an error, drains its own TMA loads and MMAs, frees its
+// tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -48,9 +48,8 @@ constexpr int kABox = kTM * kKC * 2;   // 16 KiB
 constexpr int kBBox = kTN * kKC * 2;   // 8 KiB
 constexpr int kEpiWarps = 8;      // two per TMEM lane quarter, each taking half of the tile's columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
-constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kEpiCols = kTN / 2;  // columns per epilogue thread
-constexpr int kCSm = kEpiCols / 2; // of those, prefetched into shared memory (the rest into registers)
+constexpr int kCSm = kEpiCols / 2; // of those, prefetched into shared memory (the rest load in the final pass)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
 
@@ -190,9 +189,6 @@ __device__ __forceinline__ double i64_times_pow2(long long T, int e) {
                                                      (m & 0xFFFFFFFFFFFFFull)));
 }
 
-// Arrive for a barrier of a digit group that does not exist at this slice count (keeps the
-// per-group barrier phases of all eight groups in step).
-__device__ __forceinline__ void mbar_arrive_unused(uint64_t* bar) { tc::mbar_arrive(bar); }
 
 struct SmemLayout {
   static size_t bytes(int S) {
@@ -200,13 +196,20 @@ struct SmemLayout {
   }
 };
 
-// Persistent kernel: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// Roles: warp 0 = TMA producer (U slices of the tile, then the L slices through the
+// Persistent kernel: CTA b takes the contiguous range [b T / G, (b + 1) T / G) of the T tiles
+// in column-major order, so consecutive tiles of a CTA share their U slices, which are
+// loaded again only when the tile column changes.
+// Roles: warp 0 = TMA producer (U slices of a new tile column, then the L slices through the
 // ring), warp 1 = MMA issuer, warps 2-9 = epilogue (warp w reads TMEM lanes
-// 32 (w % 4) .. + 31 and the column half (w - 2) / 4 of the tile).  Per tile: the MMA warp waits for the tile's U slices and for the
-// epilogue to have drained the previous tile's accumulators; the epilogue loads its 64 C
-// values per row into registers before waiting for the accumulators, so the C reads
-// overlap the MMAs; the U slices of the next tile load while the epilogue drains.
+// 32 (w % 4) .. + 31 and the column half (w - 2) / 4 of the tile).
+// The L slices are consumed in ascending order, so digit group g is final once slice g has
+// been consumed (its terms come from slices s <= g): the MMA warp commits group g to its own
+// barrier there, and the epilogue drains the groups one by one while the MMAs of the higher
+// groups run.  At the end of a tile the MMA warp waits once, on a shared-memory counter, for
+// the epilogue to have read the last group; the epilogue then combines and stores the tile
+// while the next tile's MMAs run.  (Waits of the MMA thread on epilogue-arrived mbarriers in
+// the middle of a tile's MMA stream measured markedly slower MMA issue on GB300; this single
+// end-of-tile wait, with the pipe about to drain anyway, did not.)
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                         int N, int mpad, int npad, int S, int nkc, int tiles_m, int tiles_n, int ts_lo, int ts_hi,
@@ -215,16 +218,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (status && *status != GJ_OK) return;
   const int tiles_n_act = tiles_n - (ts_hi - ts_lo);
   const int ntiles = tiles_m * tiles_n_act;
-  if ((int)blockIdx.x >= ntiles) return;
+  const int t_begin = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
+  const int t_end = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
+  if (t_begin >= t_end) return;
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* Bres = smem;                                   // [S][2] boxes of 8 KiB
   uint8_t* Aring = smem + (size_t)S * 2 * kBBox;          // [kStages] boxes of 16 KiB
   double* Cs = reinterpret_cast<double*>(Aring + (size_t)kStages * kABox);  // [2 halves][kCSm][kTM]
-  __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_full[kStages], bar_empty[kStages], bar_accfull,
-      bar_gfree[8], bar_fin;
+  __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_full[kStages], bar_empty[kStages], bar_gready[8],
+      bar_fin;
   __shared__ uint32_t s_tmem;
+  __shared__ uint32_t s_drained;  // epilogue warps that have read the last group, summed over tiles
   __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -235,10 +241,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&bar_full[i], 1);
       tc::mbar_init(&bar_empty[i], 1);
     }
-    tc::mbar_init(&bar_accfull, 1);
-    for (int g = 0; g < 8; ++g) tc::mbar_init(&bar_gfree[g], kEpiThreads);
+    for (int g = 0; g < 8; ++g) tc::mbar_init(&bar_gready[g], 1);
     tc::mbar_init(&bar_fin, 1);
     tc::fence_mbar_init();
+    s_drained = 0;
     s_abort = 0;
     tc::tma_prefetch_desc(&mapA);
     tc::tma_prefetch_desc(&mapB);
@@ -253,11 +259,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = s_tmem;
 
   auto tile_of = [&](int idx, int& m0, int& c0) {
-    const int tm = idx / tiles_n_act, tna = idx - tm * tiles_n_act;
+    const int tna = idx / tiles_m, tm = idx - tna * tiles_m;
     const int tn = (tna < ts_lo) ? tna : tna + (ts_hi - ts_lo);
     m0 = tm * kTM;
     c0 = tn * kTN;
   };
+  // the tile starts a new tile column (its U slices must be loaded)
+  auto new_column = [&](int idx) { return idx == t_begin || (idx % tiles_m) == 0; };
 
   int issued_uses[kStages] = {0, 0, 0, 0};
   int b_issued = 0;
@@ -265,21 +273,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- producer
       int it = 0, local = 0;
-      for (int idx = blockIdx.x; idx < ntiles && !s_abort; idx += gridDim.x, ++local) {
+      for (int idx = t_begin; idx < t_end && !s_abort; ++idx, ++local) {
         int m0, c0;
         tile_of(idx, m0, c0);
-        if (local > 0 && !tc::mbar_wait_backoff(&bar_bempty, (uint32_t)((local - 1) & 1), kWaitNs)) {
-          atomicExch(err, 10);
-          s_abort = 1;
-          break;
+        if (new_column(idx)) {
+          // the MMAs of the previous tile column must have finished reading the resident U
+          // slices (bar_bempty completes one phase per tile column that is followed by another)
+          if (b_issued > 0 && !tc::mbar_wait_backoff(&bar_bempty, (uint32_t)((b_issued - 1) & 1), kWaitNs)) {
+            atomicExch(err, 10);
+            s_abort = 1;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&bar_bfull, (uint32_t)(S * nkc * kBBox));
+          ++b_issued;
+          for (int t = 0; t < S; ++t)
+            for (int kc = 0; kc < nkc; ++kc)
+              tc::tma_load_2d(Bres + (size_t)(t * 2 + kc) * kBBox, &mapB, kc * kKC, t * npad + c0, &bar_bfull);
         }
-        tc::mbar_arrive_expect_tx(&bar_bfull, (uint32_t)(S * nkc * kBBox));
-        b_issued = local + 1;
-        for (int t = 0; t < S; ++t)
-          for (int kc = 0; kc < nkc; ++kc)
-            tc::tma_load_2d(Bres + (size_t)(t * 2 + kc) * kBBox, &mapB, kc * kKC, t * npad + c0, &bar_bfull);
         bool ok = true;
-        for (int sl = 0; sl < S && ok; ++sl)
+        for (int sl = 0; sl < S && ok; ++sl) {
           for (int kc = 0; kc < nkc; ++kc, ++it) {
             const int stage = it % kStages, use = it / kStages;
             if (use > 0 && !tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
@@ -292,21 +304,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::tma_load_2d(Aring + (size_t)stage * kABox, &mapA, kc * kKC, sl * mpad + m0, &bar_full[stage]);
             issued_uses[stage] = use + 1;
           }
+        }
         if (!ok) break;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      int it = 0, local = 0;
-      for (int idx = blockIdx.x; idx < ntiles && !s_abort; idx += gridDim.x, ++local) {
-        bool ok = tc::mbar_wait(&bar_bfull, (uint32_t)(local & 1), kWaitNs);
-        if (!ok) {
-          atomicExch(err, 20);
-          s_abort = 1;
-          break;
+      int it = 0, local = 0, b_used = 0;
+      for (int idx = t_begin; idx < t_end && !s_abort; ++idx, ++local) {
+        bool ok = true;
+        if (new_column(idx)) {
+          ok = tc::mbar_wait(&bar_bfull, (uint32_t)(b_used & 1), kWaitNs);
+          ++b_used;
+          if (!ok) {
+            atomicExch(err, 20);
+            s_abort = 1;
+            break;
+          }
+          tc::tc_fence_after();
         }
-        tc::tc_fence_after();
         for (int sl = 0; sl < S && ok; ++sl) {
           for (int kc = 0; kc < nkc; ++kc, ++it) {
             const int stage = it % kStages, use = it / kStages;
@@ -317,14 +334,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::tc_fence_after();
             const uint64_t a0 = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kABox));
             for (int t = 0; sl + t < S; ++t) {
-              if (sl == 0 && kc == 0 && local > 0) {
-                // first write of group t in this tile: the epilogue must have drained it
-                if (!tc::mbar_wait(&bar_gfree[t], (uint32_t)((local - 1) & 1), kWaitNs)) {
-                  ok = false;
-                  break;
-                }
-                tc::tc_fence_after();
-              }
               const uint32_t d = tmem + (uint32_t)(kTN * (sl + t));
               const uint64_t b0 = tc::desc_k128_sw128(tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox));
 #pragma unroll
@@ -334,14 +343,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc::mma_commit(&bar_empty[stage]);
           }
+          // digit group sl has received all of its terms
+          if (ok) tc::mma_commit(&bar_gready[sl]);
         }
         if (!ok) {
           atomicExch(err, 21);
           s_abort = 1;
           break;
         }
-        tc::mma_commit(&bar_bempty);
-        tc::mma_commit(&bar_accfull);
+        if (idx + 1 < t_end && new_column(idx + 1)) tc::mma_commit(&bar_bempty);
+        // the epilogue must have read this tile's accumulators before the next tile's MMAs
+        // overwrite them
+        const uint32_t target = (uint32_t)(kEpiWarps * (local + 1));
+        const uint64_t w0 = tc::global_timer_ns();
+        while (tc::counter_load_acquire(&s_drained) < target) {
+          if (s_abort || tc::global_timer_ns() - w0 > kWaitNs) {
+            ok = false;
+            break;
+          }
+        }
+        if (!ok) {
+          atomicExch(err, 22);
+          s_abort = 1;
+          break;
+        }
+        tc::tc_fence_after();
       }
     }
   } else {
@@ -352,65 +378,90 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16) + (uint32_t)(h * kEpiCols);
     double* Csh = Cs + (size_t)h * kCSm * kTM;
     int local = 0;
-    for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x, ++local) {
+    for (int idx = t_begin; idx < t_end; ++idx, ++local) {
       int m0, c0;
       tile_of(idx, m0, c0);
       c0 += h * kEpiCols;
       const int gi = m0 + r;
       const bool row_ok = gi < M;
-      // C for this row and column half, loaded before the accumulators are ready
-      // (overlaps the MMAs): kCSm columns into shared memory (cp.async), the rest into
-      // registers
+      // kCSm of this row's C values into shared memory now (cp.async, overlapping the MMAs);
+      // the column exponents of the warp's kEpiCols columns, one per lane
 #pragma unroll
       for (int c = 0; c < kCSm; ++c) {
         const int gj = c0 + c;
         if (row_ok && gj < N) tc::cp_async8(&Csh[c * kTM + r], &C[(int64_t)gi + (int64_t)gj * ldc]);
       }
       tc::cp_async_commit();
-      double cv[kEpiCols - kCSm];
-#pragma unroll
-      for (int c = 0; c < kEpiCols - kCSm; ++c) {
-        const int gj = c0 + kCSm + c;
-        cv[c] = (row_ok && gj < N) ? C[(int64_t)gi + (int64_t)gj * ldc] : 0.0;
-      }
+      const int ec_lane = (c0 + lane < N) ? ecol[c0 + lane] : 0;
       const int er = row_ok ? erow[gi] : 0;
-      bool ok = tc::mbar_wait_backoff(&bar_accfull, (uint32_t)(local & 1), kWaitNs);
-      ok = __all_sync(0xffffffffu, ok) && !__any_sync(0xffffffffu, s_abort != 0);
-      if (!ok) {
-        atomicExch(err, 30);
-        s_abort = 1;
-        break;
-      }
-      tc::tc_fence_after();
-      // drain the groups in order, releasing each to the next tile's MMAs as soon as it is read
+      // drain the groups in order as each becomes final
       long long T[kEpiCols];
 #pragma unroll
       for (int c = 0; c < kEpiCols; ++c) T[c] = 0;
+      bool ok = true;
       for (int g = 0; g < S; ++g) {
-        uint32_t v[kEpiCols / 8][8];
-#pragma unroll
-        for (int cc = 0; cc < kEpiCols / 8; ++cc) tc::tmem_ld8(lane_base + (uint32_t)(kTN * g + 8 * cc), v[cc]);
-        tc::tmem_ld_wait();
-        tc::tc_fence_before();
-        tc::mbar_arrive(&bar_gfree[g]);
+        // one lane polls, the warp follows
+        int ok0 = 0;
+        if (lane == 0) ok0 = tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(local & 1), kWaitNs) && !s_abort;
+        ok = __shfl_sync(0xffffffffu, ok0, 0) != 0;  // warp-uniform
+        if (!ok) break;
+        tc::tc_fence_after();
         const int sh = 55 - 7 * (g + 2);
+        // two halves of 16 columns (keeps the live registers within one CTA per SM)
 #pragma unroll
-        for (int cc = 0; cc < kEpiCols / 8; ++cc)
+        for (int half = 0; half < 2; ++half) {
+          uint32_t v[2][8];
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const long long G = static_cast<long long>(__float2int_rn(__uint_as_float(v[cc][c])));
-            T[8 * cc + c] += (sh >= 0) ? (G << sh) : (G >> (-sh));
+          for (int cc = 0; cc < 2; ++cc)
+            tc::tmem_ld8(lane_base + (uint32_t)(kTN * g + 16 * half + 8 * cc), v[cc]);
+          tc::tmem_ld_wait();
+          if (g == S - 1 && half == 1) {
+            // all of this tile's accumulators read by this warp: release them to the MMA warp
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::counter_add_release(&s_drained, 1u);
           }
-      }
-      for (int g = S; g < 8; ++g) mbar_arrive_unused(&bar_gfree[g]);
-      tc::cp_async_wait_all();
-      if (row_ok) {
 #pragma unroll
-        for (int cl = 0; cl < kEpiCols; ++cl) {
-          const int gj = c0 + cl;
-          if (gj >= N || (gj >= skip_lo && gj < skip_hi) || T[cl] == 0) continue;
-          const double cold = (cl < kCSm) ? Csh[cl * kTM + r] : cv[cl - kCSm];
-          C[(int64_t)gi + (int64_t)gj * ldc] = cold + i64_times_pow2(T[cl], er + ecol[gj] - 55);
+          for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const long long G = static_cast<long long>(__float2int_rn(__uint_as_float(v[cc][c])));
+              T[16 * half + 8 * cc + c] += (sh >= 0) ? (G << sh) : (G >> (-sh));
+            }
+        }
+      }
+      if (!ok) {
+        atomicExch(err, 30);
+        s_abort = 1;
+        tc::cp_async_wait_all();
+        break;
+      }
+      tc::cp_async_wait_all();
+      // combine and store in batches of 8 columns; each batch's old C values are loaded
+      // (from shared memory, or from global memory for the second half) before the
+      // previous batch is computed, so the loads' latency overlaps the arithmetic
+      constexpr int kB = 8;
+      double cold[2][kB];
+      auto load_batch = [&](int b, double (&dst)[kB]) {
+#pragma unroll
+        for (int c = 0; c < kB; ++c) {
+          const int cl = b * kB + c, gj = c0 + cl;
+          if (cl < kCSm)
+            dst[c] = Csh[cl * kTM + r];
+          else
+            dst[c] = (row_ok && gj < N) ? C[(int64_t)gi + (int64_t)gj * ldc] : 0.0;
+        }
+      };
+      load_batch(0, cold[0]);
+#pragma unroll
+      for (int b = 0; b < kEpiCols / kB; ++b) {
+        if (b + 1 < kEpiCols / kB) load_batch(b + 1, cold[(b + 1) & 1]);
+#pragma unroll
+        for (int c = 0; c < kB; ++c) {
+          const int cl = b * kB + c, gj = c0 + cl;
+          const int ec = __shfl_sync(0xffffffffu, ec_lane, cl);
+          if (!row_ok || gj >= N || (gj >= skip_lo && gj < skip_hi) || T[cl] == 0) continue;
+          C[(int64_t)gi + (int64_t)gj * ldc] = cold[b & 1][c] + i64_times_pow2(T[cl], er + ec - 55);
         }
       }
     }

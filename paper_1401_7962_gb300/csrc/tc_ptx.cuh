@@ -71,6 +71,18 @@ __device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity
   }
 }
 
+// Shared-memory counter with release / acquire semantics at CTA scope (a lighter
+// producer-to-consumer signal than an mbarrier when only one thread waits).
+__device__ __forceinline__ void counter_add_release(uint32_t* ctr, uint32_t v) {
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(ctr)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t counter_load_acquire(const uint32_t* ctr) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(ctr)) : "memory");
+  return v;
+}
+
 // ---------------------------------------------------------------- TMA
 
 __device__ __forceinline__ void tma_prefetch_desc(const void* map) {

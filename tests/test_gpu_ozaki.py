@@ -67,6 +67,17 @@ def test_emulated_update_within_bound(M, N, K, S):
     assert np.all(err <= bound), float(np.max(err / bound))
 
 
+@pytest.mark.parametrize("M,N,K,S", [(256, 40000, 32, 1), (256, 40000, 32, 8), (130, 30000, 128, 8),
+                                     (1100, 3000, 128, 8), (2048, 2048, 64, 3)])
+def test_emulated_update_many_tiles_per_cta(M, N, K, S):
+    """Grids of several tiles per CTA: tile columns change inside a CTA's range (the U slices
+    are reloaded), and with K <= 64 and S = 1 the producer runs tiles ahead of the MMAs."""
+    rng = np.random.default_rng(M + N + K + S)
+    got, ref, bound = run(M, N, K, S, rng)
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
 def test_emulated_update_scaled_rows_and_lda():
     rng = np.random.default_rng(11)
     got, ref, bound = run(384, 192, 128, 8, rng, ldl_pad=9, scale_rows=True)
