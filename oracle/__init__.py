@@ -64,6 +64,9 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.gjo_invert.restype = ctypes.c_int
     lib.gjo_invert.argtypes = [ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_double,
                                P, P, P, P, P, P, P]
+    lib.gjo_solve.restype = ctypes.c_int
+    lib.gjo_solve.argtypes = [ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int64, P,
+                              ctypes.c_int64, ctypes.c_int, ctypes.c_double, P, P, P, P, P, P]
     lib.gjo_invert_range.restype = None
     lib.gjo_invert_range.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, ctypes.c_int, P, P, P]
     return lib
@@ -107,6 +110,35 @@ def invert(A: np.ndarray, pivot_mode: int = PIVOT_PARTIAL, tau: float = 0.0, _li
                       ctypes.addressof(lg), _ptr(pr), _ptr(pc), _ptr(pv), _ptr(gp), ctypes.addressof(fs))
     return {"X": X, "status": st, "det_sign": sgn.value, "det_log2": lg.value, "piv_rows": pr[:n].copy(),
             "piv_cols": pc[:n].copy(), "pivots": pv[:n].copy(), "gaps": gp[:n].copy(), "fail_step": fs.value}
+
+
+def solve(A: np.ndarray, B: np.ndarray, pivot_mode: int = PIVOT_PARTIAL, tau: float = 0.0, _lib=None) -> dict:
+    """Solve A X = B with the oracle's Gauss-Jordan sweep of [A | B] (eqs. 3-10, B in the
+    place of D).  ``B`` is n x m (a 1-D vector is taken as one column).  Returns a dict with
+    ``X`` (n x m), ``status``, ``det_sign``, ``det_log2``, ``piv_rows``, ``piv_cols``,
+    ``pivots``, ``fail_step``."""
+    L = _lib if _lib is not None else lib()
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    if A.ndim != 2 or A.shape[0] != A.shape[1] or B.ndim != 2 or B.shape[0] != A.shape[0]:
+        raise ValueError("A square, B with as many rows as A")
+    n, m = A.shape[0], B.shape[1]
+    Af = np.asfortranarray(A)
+    Bf = np.asfortranarray(B)
+    X = np.zeros((n, m), dtype=np.float64, order="F")
+    sgn = ctypes.c_int(0)
+    lg = ctypes.c_double(0.0)
+    pr = np.full(max(n, 1), -1, dtype=np.int32)
+    pc = np.full(max(n, 1), -1, dtype=np.int32)
+    pv = np.zeros(max(n, 1), dtype=np.float64)
+    fs = ctypes.c_int64(-1)
+    st = L.gjo_solve(n, m, _ptr(Af), max(n, 1), _ptr(Bf) if m else None, max(n, 1), _ptr(X) if m else None,
+                     max(n, 1), pivot_mode, tau, ctypes.addressof(sgn), ctypes.addressof(lg), _ptr(pr), _ptr(pc),
+                     _ptr(pv), ctypes.addressof(fs))
+    return {"X": X, "status": st, "det_sign": sgn.value, "det_log2": lg.value, "piv_rows": pr[:n].copy(),
+            "piv_cols": pc[:n].copy(), "pivots": pv[:n].copy(), "fail_step": fs.value}
 
 
 def invert_many(sizes: np.ndarray, packed: np.ndarray, offsets: np.ndarray, pivot_mode: int = PIVOT_PARTIAL,

@@ -8,6 +8,7 @@
  * benchmark do.  It shares no code, header or table with the CUDA path.
  *
  * What it computes (Section 2 of the paper):
+ * (gjo_invert; gjo_solve applies the same steps to [A | B] for right-hand sides B, below)
  *   - initialisation A^0 = A, D^0 = I (eqs. 1-2);
  *   - n steps, each: pivot selection (observations 2-3), pivot-row scaling by the
  *     pivot (eq. 14), and elimination of the pivot column from every other row
@@ -238,4 +239,130 @@ void gjo_invert_range(int64_t m0, int64_t m1, const int32_t* n, const double* A,
     det_sign[m] = s;
     det_log2[m] = l;
   }
+}
+
+/*
+ * gjo_solve: solve A X = B for the n x n column-major A (leading dimension lda) and the
+ * n x m column-major right-hand sides B (leading dimension ldb) by the Gauss-Jordan sweep
+ * of Section 2 with B in the place of D: eqs. 3-10 with d replaced by the columns of B.
+ * At step k (after the pivot selection and interchanges of observations 2-3, chosen
+ * exactly as in gjo_invert, on the columns of A only):
+ *   eq. 3:  a_kj <- a_kj / a_kk                 for the columns j of A after k
+ *   eq. 4:  b_kj <- b_kj / a_kk                 for every column j of B
+ *   eq. 7:  a_ij <- a_ij - a_ik a_kj            for i != k, the columns j of A after k
+ *   eq. 8:  b_ij <- b_ij - a_ik b_kj            for i != k, every column j of B
+ * (column k of A becomes the unit column and is not needed again).  Row interchanges move
+ * whole rows of [A | B] and need no undoing; a column interchange of A exchanges two
+ * unknowns, so at the end the rows of the solution are exchanged back in reverse order.
+ * X (n x m, leading dimension ldx) receives A^-1 B.  Outputs and statuses as for
+ * gjo_invert.  The working array is row-major n x (n + m).
+ */
+int gjo_solve(int64_t n, int64_t m, const double* A, int64_t lda, const double* B, int64_t ldb, double* X,
+              int64_t ldx, int pivot_mode, double tau, int* det_sign, double* det_log2, int32_t* piv_rows,
+              int32_t* piv_cols, double* pivots, int64_t* fail_step) {
+  if (det_sign) *det_sign = 0;
+  if (det_log2) *det_log2 = -INFINITY;
+  if (fail_step) *fail_step = -1;
+  if (n < 0 || m < 0 || lda < (n > 0 ? n : 1) || ldb < (n > 0 ? n : 1) || ldx < (n > 0 ? n : 1) ||
+      pivot_mode < 0 || pivot_mode > 3 || !(tau >= 0.0))
+    return GJO_ERR_ARG;
+  if (n == 0) {
+    if (det_sign) *det_sign = 1;
+    if (det_log2) *det_log2 = 0.0;
+    return GJO_OK;
+  }
+  if (!A || (m > 0 && (!B || !X))) return GJO_ERR_ARG;
+
+  const int64_t w = n + m; /* row length of the working array [A | B] */
+  double* y = (double*)malloc(sizeof(double) * (size_t)n * (size_t)w);
+  int64_t* pcol = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  if (!y || !pcol) {
+    free(y); free(pcol);
+    return GJO_ERR_NOMEM;
+  }
+#define Y_(i, j) y[(size_t)(i) * (size_t)w + (size_t)(j)]
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j) Y_(i, j) = A[(size_t)i + (size_t)j * (size_t)lda];
+    for (int64_t j = 0; j < m; ++j) Y_(i, n + j) = B[(size_t)i + (size_t)j * (size_t)ldb];
+  }
+
+  int sign = 1;
+  double lg = 0.0;
+  int status = GJO_OK;
+  for (int64_t k = 0; k < n; ++k) {
+    /* ---- pivot selection over the columns of A (observations 2-3) ---- */
+    int64_t r = k, c = k;
+    double best = -1.0;
+    int nonfinite = 0;
+    if (pivot_mode == GJO_PIVOT_NONE) {
+      best = fabs(Y_(k, k));
+      if (!isfinite(Y_(k, k))) nonfinite = 1;
+    } else if (pivot_mode == GJO_PIVOT_PARTIAL) {
+      for (int64_t i = k; i < n; ++i) {
+        if (!isfinite(Y_(i, k))) nonfinite = 1;
+        if (fabs(Y_(i, k)) > best) { best = fabs(Y_(i, k)); r = i; }
+      }
+    } else if (pivot_mode == GJO_PIVOT_FULL) {
+      for (int64_t j = k; j < n; ++j) { /* column by column, each top to bottom */
+        for (int64_t i = k; i < n; ++i) {
+          if (!isfinite(Y_(i, j))) nonfinite = 1;
+          if (fabs(Y_(i, j)) > best) { best = fabs(Y_(i, j)); r = i; c = j; }
+        }
+      }
+    } else {
+      double q = 0.0;
+      for (int64_t i = k; i < n; ++i) {
+        if (!isfinite(Y_(i, k))) nonfinite = 1;
+        if (Y_(i, k) > q) { q = Y_(i, k); r = i; }
+      }
+      best = fabs(Y_(r, k));
+    }
+    if (nonfinite || !isfinite(best)) { status = GJO_NONFINITE; if (fail_step) *fail_step = k; break; }
+    if (!(best > tau)) { /* observation 2: no usable pivot */
+      status = (pivot_mode == GJO_PIVOT_NONE || pivot_mode == GJO_PIVOT_PAPER_SIGNED) ? GJO_ZERO_PIVOT
+                                                                                   : GJO_SINGULAR;
+      if (fail_step) *fail_step = k;
+      break;
+    }
+    /* ---- interchanges: whole rows of [A | B]; columns of A only ---- */
+    if (r != k) {
+      for (int64_t j = 0; j < w; ++j) { double t = Y_(k, j); Y_(k, j) = Y_(r, j); Y_(r, j) = t; }
+      sign = -sign;
+    }
+    if (c != k) {
+      for (int64_t i = 0; i < n; ++i) { double t = Y_(i, k); Y_(i, k) = Y_(i, c); Y_(i, c) = t; }
+      sign = -sign;
+    }
+    pcol[k] = c;
+    if (piv_rows) piv_rows[k] = (int32_t)r;
+    if (piv_cols) piv_cols[k] = (int32_t)c;
+    const double q = Y_(k, k);
+    if (pivots) pivots[k] = q;
+    if (q < 0.0) { sign = -sign; } /* eq. 13 */
+    lg = lg + log2(fabs(q));
+    /* ---- eqs. 3-4: the pivot row after column k, divided by the pivot ---- */
+    for (int64_t j = k + 1; j < w; ++j) Y_(k, j) = Y_(k, j) / q;
+    Y_(k, k) = 1.0;
+    /* ---- eqs. 7-8: every other row ---- */
+    for (int64_t i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double a_ik = Y_(i, k);
+      for (int64_t j = k + 1; j < w; ++j) Y_(i, j) = Y_(i, j) - a_ik * Y_(k, j);
+      Y_(i, k) = 0.0;
+    }
+  }
+  if (status == GJO_OK) {
+    /* ---- exchanged unknowns back, in reverse order ---- */
+    for (int64_t k = n - 1; k >= 0; --k)
+      if (pcol[k] != k)
+        for (int64_t j = n; j < w; ++j) { double t = Y_(k, j); Y_(k, j) = Y_(pcol[k], j); Y_(pcol[k], j) = t; }
+    for (int64_t j = 0; j < m; ++j)
+      for (int64_t i = 0; i < n; ++i) X[(size_t)i + (size_t)j * (size_t)ldx] = Y_(i, n + j);
+    if (det_sign) *det_sign = sign;
+    if (det_log2) *det_log2 = lg;
+  }
+#undef Y_
+  free(y);
+  free(pcol);
+  return status;
 }

@@ -2,7 +2,8 @@
 
 Every pin takes ``inv(A, mode, tau=0.0) -> dict`` (the oracle's result dict:
 X, status, det_sign, det_log2, piv_rows, piv_cols, pivots, fail_step) and raises
-AssertionError when the inverter disagrees.  The expected values never come from
+AssertionError when the inverter disagrees.  The solve pins (``ALL_SOLVE_PINS``) take
+``sol(A, B, mode, tau=0.0) -> dict`` with the same keys, X being A^-1 B.  The expected values never come from
 the inverter under test: they are closed forms (symmetric Pascal and Hilbert
 inverses and determinants), exact integer arithmetic (cofactor expansion,
 Fraction forward substitution), special matrices (permutations, diagonal,
@@ -392,3 +393,149 @@ def pin_failures(inv):
 ALL_PINS = [pin_paper_example, pin_pascal, pin_hilbert, pin_cofactor_det, pin_permutation, pin_diagonal,
             pin_triangular, pin_orthogonal, pin_invariants_random, pin_numpy_crosscheck, pin_pivot_rule,
             pin_tie_rule, pin_diag_dominant_identity, pin_row_swap_flips_det, pin_failures]
+
+
+# ---------------------------------------------------------------- solve pins (A X = B)
+
+def _int_rhs(n: int, m: int, seed: int) -> list[list[int]]:
+    g = _rng(seed)
+    return [[int(v) for v in row] for row in g.integers(-9, 10, size=(n, m))]
+
+
+def _matmul_int(P, Q):
+    return [[sum(P[i][t] * Q[t][j] for t in range(len(Q))) for j in range(len(Q[0]))] for i in range(len(P))]
+
+
+def pin_solve_paper_example(sol):
+    """Section 3 matrix: b = A (1, 2, 3)^T gives x = (1, 2, 3) (exactly where the pivots are dyadic); with
+    B = I the sweep returns the integer inverse; pivot sequences are the hand-run ones."""
+    with open(os.path.join(GOLDEN, "paper_example_3x3.json")) as f:
+        g = json.load(f)
+    A = np.array(g["A"], dtype=np.float64)
+    b = A @ np.array([1.0, 2.0, 3.0])
+    for name, exp in g["modes"].items():
+        r = sol(A, b[:, None], MODES[name])
+        assert r["status"] == OK, (name, r["status"])
+        if exp["exact"]:  # dyadic pivots: every intermediate is exact
+            assert np.array_equal(r["X"][:, 0], [1.0, 2.0, 3.0]), (name, r["X"])
+        else:
+            assert np.max(np.abs(r["X"][:, 0] - [1.0, 2.0, 3.0])) <= 16 * EPS * 25, (name, r["X"])
+        assert r["det_sign"] == 1 and abs(r["det_log2"]) <= 8 * EPS, name
+        assert list(r["piv_rows"]) == exp["piv_rows"], (name, r["piv_rows"])
+        assert list(r["piv_cols"]) == exp["piv_cols"], (name, r["piv_cols"])
+        r = sol(A, np.eye(3), MODES[name])
+        assert np.max(np.abs(r["X"] - np.array(g["inverse"]))) <= 16 * EPS * 6, (name, r["X"])
+
+
+def pin_solve_pascal(sol):
+    """Symmetric Pascal P_n with integer right-hand sides: X = P^-1 B exactly in integers."""
+    for n in range(1, 13):
+        P = pascal_sym(n)
+        Bi = _int_rhs(n, 3, 100 + n)
+        Xe = np.array(_matmul_int(pascal_sym_inverse(n), Bi), dtype=np.float64)
+        Pf = np.array(P, dtype=np.float64)
+        kappa = np.linalg.norm(Pf, 1) * np.linalg.norm(np.array(pascal_sym_inverse(n), dtype=np.float64), 1)
+        for mode in (1, 2):
+            r = sol(Pf, np.array(Bi, dtype=np.float64), mode)
+            assert r["status"] == OK
+            scale = np.linalg.norm(np.array(pascal_sym_inverse(n), dtype=np.float64), 1) * \
+                np.max(np.abs(np.array(Bi, dtype=np.float64))) * 3
+            err = np.max(np.abs(r["X"] - Xe)) / max(scale, 1.0)
+            assert err <= max(50 * n * kappa * EPS, 4 * EPS), (n, mode, err)
+
+
+def pin_solve_hilbert(sol):
+    """Hilbert H_n: X = H^-1 B with the closed-form integer inverse; det c_n^4 / c_2n."""
+    for n in range(1, 9):
+        H = np.array([[1.0 / (i + j + 1) for j in range(n)] for i in range(n)])
+        Hi = hilbert_inverse(n)
+        Bi = _int_rhs(n, 2, 200 + n)
+        Xe = np.array(_matmul_int(Hi, Bi), dtype=np.float64)
+        Hif = np.array(Hi, dtype=np.float64)
+        kappa = np.linalg.norm(H, 1) * np.linalg.norm(Hif, 1)
+        for mode in (1, 2):
+            r = sol(H, np.array(Bi, dtype=np.float64), mode)
+            assert r["status"] == OK
+            err = np.max(np.abs(r["X"] - Xe)) / max(np.max(np.abs(Xe)), 1.0)
+            assert err <= 100 * n * kappa * EPS, (n, mode, err)
+            want = math.log2(hilbert_det(n))
+            assert abs(r["det_log2"] - want) <= 1e-9 * max(1.0, abs(want)), (n, mode)
+
+
+def pin_solve_exact_fraction(sol):
+    """Integer matrices n <= 6: X = A^-1 B from exact Fraction elimination; det by cofactors."""
+    g = _rng(31)
+    for n in range(1, 7):
+        for _ in range(3):
+            M = [[int(v) for v in row] for row in g.integers(-9, 10, size=(n, n))]
+            d = det_cofactor(M)
+            if d == 0:
+                continue
+            Bi = _int_rhs(n, 2, 300 + n)
+            Mi = inverse_fraction(M)
+            Xe = np.array([[float(sum(Mi[i][t] * Bi[t][j] for t in range(n))) for j in range(2)]
+                           for i in range(n)])
+            A = np.array(M, dtype=np.float64)
+            kappa = np.linalg.norm(A, 1) * np.linalg.norm(np.array([[float(v) for v in row] for row in Mi]), 1)
+            for mode in (1, 2):
+                r = sol(A, np.array(Bi, dtype=np.float64), mode)
+                assert r["status"] == OK
+                err = np.max(np.abs(r["X"] - Xe)) / max(np.max(np.abs(Xe)), 1.0)
+                assert err <= 50 * n * kappa * EPS, (n, mode, err)
+                assert r["det_sign"] == (1 if d > 0 else -1)
+                assert log2_close(r["det_log2"], math.log2(abs(d)), 1e-12)
+
+
+def pin_solve_permutation(sol):
+    """A permutation matrix: X = P^T B exactly, det = sign of the permutation."""
+    g = _rng(41)
+    for n in (1, 2, 5, 9):
+        p = g.permutation(n)
+        P = np.zeros((n, n))
+        P[np.arange(n), p] = 1.0
+        B = g.standard_normal((n, 3))
+        for mode in (1, 2):
+            r = sol(P, B, mode)
+            assert r["status"] == OK and np.array_equal(r["X"], P.T @ B), (n, mode)
+            assert r["det_sign"] == perm_sign(list(p))
+
+
+def pin_solve_invariants(sol):
+    """Random inputs: A X = B at the residual level, solve(A, A) = I, and the pivot sequence
+    of the sweep does not depend on the right-hand sides."""
+    g = _rng(51)
+    for n in (2, 9, 40):
+        A = g.standard_normal((n, n)) + 0.5 * np.eye(n)
+        B = g.standard_normal((n, 4))
+        for mode in (1, 2):
+            r = sol(A, B, mode)
+            assert r["status"] == OK
+            res = np.linalg.norm(A @ r["X"] - B) / (np.linalg.norm(A) * np.linalg.norm(r["X"]) + np.linalg.norm(B))
+            assert res <= 50 * n * EPS, (n, mode, res)
+            r2 = sol(A, A, mode)
+            assert np.max(np.abs(r2["X"] - np.eye(n))) <= 1e-10, (n, mode)
+            r3 = sol(A, B[:, :1], mode)
+            assert list(r3["piv_rows"]) == list(r["piv_rows"]) and list(r3["piv_cols"]) == list(r["piv_cols"])
+            ref = np.linalg.solve(A, B)
+            assert np.max(np.abs(r["X"] - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref))), (n, mode)
+
+
+def pin_solve_failures(sol):
+    """Observation 2 for the solve: zero pivot vs singular, non-finite input, no right-hand side."""
+    S = np.array([[0.0, 1.0], [1.0, 0.0]])
+    b = np.array([[2.0], [3.0]])
+    assert sol(S, b, 0)["status"] == ZERO_PIVOT
+    r = sol(S, b, 1)
+    assert r["status"] == OK and np.array_equal(r["X"], np.array([[3.0], [2.0]])) and r["det_sign"] == -1
+    Z = np.array([[1.0, 2.0, 0.0], [3.0, 4.0, 0.0], [5.0, 6.0, 0.0]])
+    r = sol(Z, np.ones((3, 1)), 1)
+    assert r["status"] == SINGULAR and r["fail_step"] == 2 and r["det_sign"] == 0 and r["det_log2"] == -math.inf
+    N = np.eye(3)
+    N[1, 0] = np.nan
+    assert sol(N, np.ones((3, 1)), 1)["status"] == NONFINITE
+    r = sol(np.array([[2.0, 0.0], [0.0, 4.0]]), np.zeros((2, 0)), 1)
+    assert r["status"] == OK and r["det_sign"] == 1 and r["det_log2"] == 3.0
+
+
+ALL_SOLVE_PINS = [pin_solve_paper_example, pin_solve_pascal, pin_solve_hilbert, pin_solve_exact_fraction,
+                  pin_solve_permutation, pin_solve_invariants, pin_solve_failures]

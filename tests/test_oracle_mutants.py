@@ -41,6 +41,22 @@ MUTANTS = {
 }
 
 
+# mistakes in the solve sweep (gjo_solve), caught by the solve pins
+SOLVE_MUTANTS = {
+    "solve_eq8_sign": ("for (int64_t j = k + 1; j < w; ++j) Y_(i, j) = Y_(i, j) - a_ik * Y_(k, j);",
+                       "for (int64_t j = k + 1; j < w; ++j) Y_(i, j) = Y_(i, j) + a_ik * Y_(k, j);"),
+    "solve_eq4_skips_B": ("for (int64_t j = k + 1; j < w; ++j) Y_(k, j) = Y_(k, j) / q;",
+                          "for (int64_t j = k + 1; j < n; ++j) Y_(k, j) = Y_(k, j) / q;"),
+    "solve_row_swap_A_only": ("for (int64_t j = 0; j < w; ++j) { double t = Y_(k, j);",
+                              "for (int64_t j = 0; j < n; ++j) { double t = Y_(k, j);"),
+    "solve_unknowns_not_restored": ("      if (pcol[k] != k)\n        for (int64_t j = n; j < w; ++j)",
+                                    "      if (0)\n        for (int64_t j = n; j < w; ++j)"),
+    "solve_restore_forward": ("    for (int64_t k = n - 1; k >= 0; --k)\n      if (pcol[k] != k)",
+                              "    for (int64_t k = 0; k < n; ++k)\n      if (pcol[k] != k)"),
+    "solve_det_sign_of_pivot": ("    if (q < 0.0) { sign = -sign; } /* eq. 13 */", "    /* eq. 13 */"),
+}
+
+
 @functools.lru_cache(maxsize=None)
 def _source():
     return oracle.source()
@@ -65,3 +81,22 @@ def test_mutant_is_caught(name, tmp_path):
         except (ValueError, FloatingPointError, ZeroDivisionError, OverflowError):
             failures.append(pin.__name__)
     assert failures, f"no pin catches mutant {name}"
+
+
+@pytest.mark.parametrize("name", sorted(SOLVE_MUTANTS))
+def test_solve_mutant_is_caught(name, tmp_path):
+    old, new = SOLVE_MUTANTS[name]
+    src = _source()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique in the oracle source"
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / f"libmut_{name}.so"))
+
+    def sol(A, B, mode, tau=0.0):
+        return oracle.solve(A, B, mode, tau, _lib=lib)
+
+    failures = []
+    for pin in pins.ALL_SOLVE_PINS:
+        try:
+            pin(sol)
+        except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError, OverflowError):
+            failures.append(pin.__name__)
+    assert failures, f"no solve pin catches mutant {name}"

@@ -14,6 +14,15 @@ def test_oracle_pin(pin):
     pin(_inv)
 
 
+def _sol(A, B, mode, tau=0.0):
+    return oracle.solve(A, B, mode, tau)
+
+
+@pytest.mark.parametrize("pin", pins.ALL_SOLVE_PINS, ids=lambda p: p.__name__)
+def test_oracle_solve_pin(pin):
+    pin(_sol)
+
+
 def test_oracle_batched_matches_single():
     """The batched oracle entry runs the same per-matrix inversion."""
     import numpy as np
