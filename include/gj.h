@@ -108,6 +108,36 @@ gj_status gj_invert_ex(const gj_opts* opts, int64_t n, const double* A, int64_t 
                        int pivot_mode, int* det_sign, double* det_log2);
 
 /*
+ * gj_solve -- solve A X = B by one Gauss-Jordan sweep of [A | B]: eqs. 3-10 of Section 2
+ * with the columns of B in the place of D (each step scales the pivot row of A and B by
+ * the pivot and eliminates the pivot column from every other row), pivoting as in
+ * obs. 2-3 on the columns of A, exchanged unknowns restored at the end (obs. 3).  The
+ * inverse itself is not formed.  det A (eq. 13) is returned as for gj_invert.
+ *   n          order of A, n >= 0.  n == 0 returns GJ_OK with det_sign = 1, det_log2 = 0.
+ *   nrhs       number of right-hand sides m >= 0 (m == 0: only det A is computed).
+ *   A          [lda * n] input, host or device, column-major.  Not modified.
+ *   B          [ldb * m] right-hand sides, host or device, column-major.  Not modified
+ *              unless X == B.
+ *   X          [ldx * m] output A^-1 B, host or device, column-major.  X == B is allowed
+ *              when ldx == ldb.  Contents unspecified when the status is not GJ_OK.
+ *   lda, ldb, ldx >= max(1, n).
+ *   pivot_mode a gj_pivot value: none / partial run the blocked path (cluster panels and
+ *              rank-b updates of the columns right of each panel and of B; tensor-core
+ *              update for n >= 512 unless opts->update says otherwise), full runs the
+ *              unblocked path.
+ *   det_sign, det_log2  as for gj_invert.
+ * Synchronous.  Status codes as for gj_invert; GJ_ERR_ARG also for opts->path == 1 (the
+ * single-CTA kernel does not take right-hand sides).
+ */
+gj_status gj_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* B, int64_t ldb, double* X,
+                   int64_t ldx, int pivot_mode, int* det_sign, double* det_log2);
+
+/* gj_solve_ex -- gj_solve with options (stream, tau, path 2 or 3, update engine, pivot
+ * record).  opts may be NULL.  Synchronous with respect to the host. */
+gj_status gj_solve_ex(const gj_opts* opts, int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* B,
+                      int64_t ldb, double* X, int64_t ldx, int pivot_mode, int* det_sign, double* det_log2);
+
+/*
  * gj_invert_batched -- invert `count` independent matrices of uneven orders in one
  * persistent launch (one CTA per matrix; work items taken largest order first).
  *   count      number of matrices, >= 0.

@@ -56,6 +56,10 @@ def lib() -> ctypes.CDLL:
     L.gj_invert.argtypes = [I64, P, I64, P, I, P, P]
     L.gj_invert_ex.restype = I
     L.gj_invert_ex.argtypes = [ctypes.POINTER(_Opts), I64, P, I64, P, I, P, P]
+    L.gj_solve.restype = I
+    L.gj_solve.argtypes = [I64, I64, P, I64, P, I64, P, I64, I, P, P]
+    L.gj_solve_ex.restype = I
+    L.gj_solve_ex.argtypes = [ctypes.POINTER(_Opts), I64, I64, P, I64, P, I64, P, I64, I, P, P]
     L.gj_invert_batched.restype = I
     L.gj_invert_batched.argtypes = [I64, I32, P, P, P, I, P, P, P, P]
     L.gj_invert_batched_noalloc.restype = I
@@ -188,6 +192,79 @@ def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, pa
                         ctypes.addressof(lg))
     if st < 0:
         raise GJError(st, "gj_invert_ex")
+    res = {"X": out, "status": st, "det_sign": sgn.value, "det_log2": lg.value, "fail_step": fs.value}
+    if record:
+        for k in ("piv_rows", "piv_cols", "pivots"):
+            res[k] = rec[k][:n].copy()
+    return res
+
+
+def _rhs_ld(B, n) -> tuple[int, int]:
+    """(m, ldb) of an n x m column-major float64 array."""
+    if B.ndim != 2 or int(B.shape[0]) != n:
+        raise ValueError("right-hand sides must be a 2-D array with n rows")
+    m = int(B.shape[1])
+    if _is_torch(B):
+        if B.dtype.__repr__() != "torch.float64":
+            raise TypeError("float64 right-hand sides expected")
+        s0, s1 = B.stride()
+    else:
+        if str(B.dtype) != "float64":
+            raise TypeError("float64 right-hand sides expected")
+        s0, s1 = (B.strides[0] // 8, B.strides[1] // 8)
+    ld = max(n, 1)
+    if m > 1 and n > 0:
+        if (n > 1 and s0 != 1) or s1 < n:
+            raise ValueError("right-hand sides must be column-major (row stride 1, column stride >= n)")
+        ld = int(s1)
+    return m, ld
+
+
+def solve(A, B, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, path: int = PATH_AUTO,
+          panel: int = 0, update: int = UPDATE_AUTO, slices: int = 0, stream=None, record: bool = False):
+    """Solve ``A X = B`` with ``gj_solve_ex`` (one Gauss-Jordan sweep of ``[A | B]``).
+
+    ``A`` (n x n) and ``B`` (n x m) column-major float64, host or device; ``out`` (n x m,
+    column-major) is allocated like ``B`` when omitted (``out is B`` solves in place).
+    Returns a dict: ``X``, ``status``, ``det_sign``, ``det_log2``, ``fail_step`` and, with
+    ``record=True``, ``piv_rows``, ``piv_cols``, ``pivots``.
+    """
+    import numpy as np
+    L = lib()
+    n, lda = _colmajor_ld(A)
+    m, ldb = _rhs_ld(B, n)
+    if out is None:
+        if _is_torch(B):
+            import torch
+            out = torch.empty((m, n), dtype=torch.float64, device=B.device).t()
+        else:
+            out = np.empty((n, m), dtype=np.float64, order="F")
+    mo, ldx = _rhs_ld(out, n)
+    if mo != m:
+        raise ValueError("out must be n x m")
+    o = _Opts()
+    o.stream = _stream_handle(stream)
+    o.tau = float(tau)
+    o.panel = int(panel)
+    o.path = int(path)
+    o.update = int(update)
+    o.slices = int(slices)
+    rec = {}
+    fs = ctypes.c_int64(-1)
+    if record:
+        rec["piv_rows"] = np.full(max(n, 1), -1, dtype=np.int32)
+        rec["piv_cols"] = np.full(max(n, 1), -1, dtype=np.int32)
+        rec["pivots"] = np.zeros(max(n, 1), dtype=np.float64)
+        o.piv_rows = rec["piv_rows"].ctypes.data
+        o.piv_cols = rec["piv_cols"].ctypes.data
+        o.pivots = rec["pivots"].ctypes.data
+    o.fail_step = ctypes.addressof(fs)
+    sgn = ctypes.c_int(0)
+    lg = ctypes.c_double(0.0)
+    st = L.gj_solve_ex(ctypes.byref(o), n, m, _ptr(A), lda, _ptr(B) if m else None, ldb, _ptr(out) if m else None,
+                       ldx, int(pivot_mode), ctypes.addressof(sgn), ctypes.addressof(lg))
+    if st < 0:
+        raise GJError(st, "gj_solve_ex")
     res = {"X": out, "status": st, "det_sign": sgn.value, "det_log2": lg.value, "fail_step": fs.value}
     if record:
         for k in ("piv_rows", "piv_cols", "pivots"):

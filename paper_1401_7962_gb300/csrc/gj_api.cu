@@ -226,6 +226,126 @@ gj_status gj_invert(int64_t n, const double* A, int64_t lda, double* Ainv, int p
   return gj_invert_ex(nullptr, n, A, lda, Ainv, pivot_mode, det_sign, det_log2);
 }
 
+gj_status gj_solve_ex(const gj_opts* opts, int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* B,
+                      int64_t ldb, double* X, int64_t ldx, int pivot_mode, int* det_sign, double* det_log2) {
+  gj_opts o{};
+  if (opts) o = *opts;
+  g_last_error[0] = '\0';
+  if (det_sign) *det_sign = 0;
+  if (det_log2) *det_log2 = -INFINITY;
+  if (o.fail_step) *o.fail_step = -1;
+  const int64_t ld_min = n > 0 ? n : 1;
+  if (n < 0 || nrhs < 0 || lda < ld_min || ldb < ld_min || ldx < ld_min) return GJ_ERR_ARG;
+  if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
+  if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
+  if (o.path < 0 || o.path > 3 || o.path == 1 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8)
+    return GJ_ERR_ARG;
+  if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
+  if (n == 0) {
+    if (det_sign) *det_sign = 1;
+    if (det_log2) *det_log2 = 0.0;
+    return GJ_OK;
+  }
+  if (!A || (nrhs > 0 && (!B || !X))) return GJ_ERR_ARG;
+  if (nrhs > 0 && (const void*)X == (const void*)B && ldx != ldb) return GJ_ERR_ARG;
+  if (n > 46340 || n + nrhs > 0x3fffffff) return GJ_ERR_UNSUPPORTED;
+  int path = o.path;
+  if (path == 0) path = (pivot_mode == GJ_PIVOT_FULL) ? 3 : 2;
+  if (path == 2 && pivot_mode == GJ_PIVOT_FULL) return GJ_ERR_UNSUPPORTED;
+
+  cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+  gj_status result;
+  {
+    Scratch scr(s);
+    const double* dA = A;
+    const double* dB = B;
+    double* dX = X;
+    int64_t dlda = lda, dldb = ldb, dldx = ldx;
+    const bool x_dev = nrhs == 0 || is_device_ptr(X);
+    if (!is_device_ptr(A)) {
+      double* t;
+      GJ_TRY(scr.alloc(&t, (size_t)n * (size_t)n));
+      GJ_CUDA(cudaMemcpy2DAsync(t, sizeof(double) * n, A, sizeof(double) * lda, sizeof(double) * n, n,
+                                cudaMemcpyHostToDevice, s));
+      dA = t;
+      dlda = n;
+    }
+    if (nrhs > 0 && !is_device_ptr(B)) {
+      double* t;
+      GJ_TRY(scr.alloc(&t, (size_t)n * (size_t)nrhs));
+      GJ_CUDA(cudaMemcpy2DAsync(t, sizeof(double) * n, B, sizeof(double) * ldb, sizeof(double) * n, nrhs,
+                                cudaMemcpyHostToDevice, s));
+      dB = t;
+      dldb = n;
+    }
+    if (!x_dev) {
+      GJ_TRY(scr.alloc(&dX, (size_t)n * (size_t)nrhs));
+      dldx = n;
+    }
+    int32_t* d_pr = nullptr;
+    int32_t* d_pc = nullptr;
+    double* d_pv = nullptr;
+    const bool pr_dev = is_device_ptr(o.piv_rows), pc_dev = is_device_ptr(o.piv_cols),
+               pv_dev = is_device_ptr(o.pivots);
+    if (o.piv_rows) {
+      if (pr_dev) d_pr = o.piv_rows;
+      else GJ_TRY(scr.alloc(&d_pr, (size_t)n));
+    }
+    if (o.piv_cols) {
+      if (pc_dev) d_pc = o.piv_cols;
+      else GJ_TRY(scr.alloc(&d_pc, (size_t)n));
+    }
+    if (o.pivots) {
+      if (pv_dev) d_pv = o.pivots;
+      else GJ_TRY(scr.alloc(&d_pv, (size_t)n));
+    }
+    ResultBlock* d_res;
+    GJ_TRY(scr.alloc(&d_res, 1));
+    GJ_CUDA(cudaMemsetAsync(d_res, 0, sizeof(ResultBlock), s));
+    CtaOut out{};
+    out.status = &d_res->status;
+    out.det_sign = &d_res->det_sign;
+    out.det_log2 = &d_res->det_log2;
+    out.fail_step = &d_res->fail_step;
+    out.piv_rows = d_pr;
+    out.piv_cols = d_pc;
+    out.pivots = d_pv;
+    Rhs rhs;
+    rhs.m = nrhs;
+    rhs.B = dB;
+    rhs.ldb = dldb;
+    rhs.X = dX;
+    rhs.ldx = dldx;
+    if (path == 2)
+      GJ_TRY(run_blocked(n, dA, dlda, nullptr, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s, &rhs));
+    else
+      GJ_TRY(run_unblocked(n, dA, dlda, nullptr, pivot_mode, o.tau, out, s, &rhs));
+
+    ResultBlock h{};
+    GJ_CUDA(cudaMemcpyAsync(&h, d_res, sizeof(ResultBlock), cudaMemcpyDeviceToHost, s));
+    if (!x_dev)
+      GJ_CUDA(cudaMemcpy2DAsync(X, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, nrhs,
+                                cudaMemcpyDeviceToHost, s));
+    if (o.piv_rows && !pr_dev) GJ_CUDA(cudaMemcpyAsync(o.piv_rows, d_pr, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    if (o.piv_cols && !pc_dev) GJ_CUDA(cudaMemcpyAsync(o.piv_cols, d_pc, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    if (o.pivots && !pv_dev) GJ_CUDA(cudaMemcpyAsync(o.pivots, d_pv, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    GJ_CUDA(cudaStreamSynchronize(s));
+    result = (gj_status)h.status;
+    if (result == GJ_OK) {
+      if (det_sign) *det_sign = h.det_sign;
+      if (det_log2) *det_log2 = h.det_log2;
+    }
+    if (o.fail_step) *o.fail_step = h.fail_step;
+  }
+  GJ_CUDA(cudaStreamSynchronize(s));  // scratch frees are stream-ordered
+  return result;
+}
+
+gj_status gj_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* B, int64_t ldb, double* X,
+                   int64_t ldx, int pivot_mode, int* det_sign, double* det_log2) {
+  return gj_solve_ex(nullptr, n, nrhs, A, lda, B, ldb, X, ldx, pivot_mode, det_sign, det_log2);
+}
+
 gj_status gj_invert_batched(int64_t count, int32_t nmax, const int32_t* n, const double* const* A,
                             double* const* Ainv, int pivot_mode, int32_t* status, int8_t* det_sign,
                             double* det_log2, void* stream) {

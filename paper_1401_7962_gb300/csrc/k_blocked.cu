@@ -542,6 +542,31 @@ __global__ void unpermute_kernel(int n, const double* __restrict__ W, const int*
   }
 }
 
+// Right-hand sides appended to the working array: W[:, n + j] = B[:, j].
+__global__ void copy_rhs_kernel(int n, int64_t m, const double* __restrict__ B, int64_t ldb,
+                                double* __restrict__ Wb) {
+  const int64_t total = (int64_t)n * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, i = e - j * n;
+    Wb[e] = B[i + j * ldb];
+  }
+}
+
+// Solution of A X = B after the sweep: unknown i was eliminated at position poscol[i]
+// (identity without column pivoting) by the row that holds it, rowat[position], so
+// X[i, j] = W[rowat[poscol[i]], n + j].
+__global__ void gather_solution_kernel(int n, int64_t m, const double* __restrict__ Wb,
+                                       const int* __restrict__ rowat, const int* __restrict__ poscol,
+                                       double* __restrict__ X, int64_t ldx, const int32_t* status) {
+  if (*status != GJ_OK) return;
+  const int64_t total = (int64_t)n * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n;
+    const int i = (int)(e - j * n);
+    X[i + j * ldx] = Wb[(int64_t)rowat[poscol ? poscol[i] : i] + j * n];
+  }
+}
+
 // eq. 13: sign and log2|det| from the recorded pivots and interchanges.
 __global__ void __launch_bounds__(1024) det_kernel(int n, const double* __restrict__ pivots,
                                                    const int* __restrict__ piv_rows, const int* __restrict__ piv_cols,
@@ -628,7 +653,8 @@ __global__ void __launch_bounds__(256) scan0_kernel(int n, const double* __restr
   }
 }
 
-__global__ void __launch_bounds__(1024) decide_kernel(int n, int k, int G, const uint64_t* cand_v, const int* cand_k,
+__global__ void __launch_bounds__(1024) decide_kernel(int n, int nw, int k, int G, const uint64_t* cand_v,
+                                                      const int* cand_k,
                                                       const double* __restrict__ W, int* rowat, int* colat,
                                                       int* posrow, int* poscol, double* prow, double* lcol,
                                                       StepState* ss, double* pivots, int* piv_rows, int* piv_cols,
@@ -700,13 +726,13 @@ __global__ void __launch_bounds__(1024) decide_kernel(int n, int k, int G, const
   if (!s_ok) return;
   const int R = s_R, C = s_C;
   const double inv_q = s_inv;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
     prow[j] = (j == C) ? inv_q : W[(int64_t)R + (int64_t)j * n] * inv_q;
-    lcol[j] = (j == R) ? 0.0 : W[(int64_t)j + (int64_t)C * n];
+    if (j < n) lcol[j] = (j == R) ? 0.0 : W[(int64_t)j + (int64_t)C * n];
   }
 }
 
-__global__ void __launch_bounds__(256) rank1_kernel(int n, int k, double* __restrict__ W,
+__global__ void __launch_bounds__(256) rank1_kernel(int n, int nw, int k, double* __restrict__ W,
                                                     const double* __restrict__ prow, const double* __restrict__ lcol,
                                                     const StepState* ss, const int* __restrict__ posrow,
                                                     const int* __restrict__ poscol, uint64_t* cand_v, int* cand_k,
@@ -717,7 +743,7 @@ __global__ void __launch_bounds__(256) rank1_kernel(int n, int k, double* __rest
   const bool search = kn < n;
   uint64_t bv = 0;
   int bk = kNoKey;
-  const int64_t total = (int64_t)n * n;
+  const int64_t total = (int64_t)n * nw;  // columns of A, then the right-hand sides
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
     double nv;
@@ -728,7 +754,7 @@ __global__ void __launch_bounds__(256) rank1_kernel(int n, int k, double* __rest
       nv = fma(-lcol[i], prow[j], base);
     }
     W[e] = nv;
-    if (search) {
+    if (search && j < n) {
       const int pr = posrow[i];
       if (mode == GJ_PIVOT_PARTIAL) {
         if (j == kn && pr >= kn && key_better(abs_bits(nv), pr, bv, bk)) {
@@ -831,9 +857,13 @@ static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* 
 }
 
 gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int pivot_mode, double tau, int panel,
-                      int update, int slices, const CtaOut& out, cudaStream_t s) {
+                      int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs) {
   if (n64 > 46340) return GJ_ERR_UNSUPPORTED;
   const int n = (int)n64;
+  const int64_t m = rhs ? rhs->m : 0;
+  if (n + m > 0x3fffffff) return GJ_ERR_UNSUPPORTED;
+  const int nw = (int)(n + m);  // columns of the working array: A, then the right-hand sides
+  const bool solving = rhs != nullptr;
   int cs = 1, b = 32, rp = n;
   const size_t smem = choose_panel(n, panel, &cs, &b, &rp);
   // Outer panel width: the tensor-core update takes 128-column panels, reduced as
@@ -848,9 +878,9 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   int *posrow, *rowat, *prow_ids, *piv_rows = out.piv_rows;
   void* oz_ws = nullptr;
   int32_t* oz_err = nullptr;
-  GJ_WS(W, (size_t)n * n);
+  GJ_WS(W, (size_t)n * nw);
   GJ_WS(Lbuf, (size_t)n * b);
-  GJ_WS(U, (size_t)n * b);
+  GJ_WS(U, (size_t)nw * b);
   GJ_WS(posrow, (size_t)n);
   GJ_WS(rowat, (size_t)n);
   GJ_WS(prow_ids, (size_t)Bw);
@@ -859,7 +889,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   GJ_WS(oz_err, 4);
   if (tc) {
     uint8_t* p8;
-    GJ_WS(p8, ozaki_workspace_bytes(n, n, S));
+    GJ_WS(p8, ozaki_workspace_bytes(n, nw, S));
     oz_ws = p8;
   }
   if (!pivots) GJ_WS(pivots, (size_t)n);
@@ -869,8 +899,16 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   const int sms = num_sms();
   copy_in_kernel<<<sms * 8, 256, 0, s>>>(n, A, lda, W);
   GJ_CUDA(cudaGetLastError());
+  if (m > 0) {
+    copy_rhs_kernel<<<sms * 8, 256, 0, s>>>(n, m, rhs->B, rhs->ldb, W + (size_t)n * n);
+    GJ_CUDA(cudaGetLastError());
+  }
   init_positions_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, posrow, nullptr, nullptr, nullptr);
   GJ_CUDA(cudaGetLastError());
+  if (out.piv_cols) {  // no column interchanges on this path: position k stays at k
+    init_positions_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, out.piv_cols, nullptr, nullptr, nullptr);
+    GJ_CUDA(cudaGetLastError());
+  }
 
   GJ_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (cs > 8) GJ_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -936,21 +974,39 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
         if (st != GJ_OK) return st;
       }
     }
-    if (BB == n) continue;  // one panel covers every column: nothing outside it
-    if (tc) {
-      gj_status st = ozaki_update(n, n, BB, W + (size_t)K0 * n, n, prow_ids, W, n, prow_ids, K0, K0 + BB, W, n, S,
-                                  oz_ws, oz_err, out.status, s);
-      if (st != GJ_OK) return st;
+    if (!solving) {
+      if (BB == n) continue;  // one panel covers every column: nothing outside it
+      if (tc) {
+        gj_status st = ozaki_update(n, n, BB, W + (size_t)K0 * n, n, prow_ids, W, n, prow_ids, K0, K0 + BB, W, n, S,
+                                    oz_ws, oz_err, out.status, s);
+        if (st != GJ_OK) return st;
+      } else {
+        gj_status st = fp64_update(K0, BB, 0, n, prow_ids);
+        if (st != GJ_OK) return st;
+      }
     } else {
-      gj_status st = fp64_update(K0, BB, 0, n, prow_ids);
-      if (st != GJ_OK) return st;
+      // solving: only the columns right of the panel (and the right-hand sides) matter
+      const int c0 = K0 + BB;
+      if (c0 >= nw) continue;
+      if (tc) {
+        gj_status st = ozaki_update(n, nw - c0, BB, W + (size_t)K0 * n, n, prow_ids, W + (size_t)c0 * n, n, prow_ids,
+                                    0, 0, W + (size_t)c0 * n, n, S, oz_ws, oz_err, out.status, s);
+        if (st != GJ_OK) return st;
+      } else {
+        gj_status st = fp64_update(K0, BB, c0, nw, prow_ids);
+        if (st != GJ_OK) return st;
+      }
     }
   }
   fold_error_kernel<<<1, 1, 0, s>>>(oz_err, out.status);
   GJ_CUDA(cudaGetLastError());
   rowat_from_posrow_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, posrow, rowat, out.status);
   GJ_CUDA(cudaGetLastError());
-  unpermute_kernel<<<sms * 8, 256, 0, s>>>(n, W, rowat, posrow, nullptr, nullptr, X, out.status);
+  if (!solving)
+    unpermute_kernel<<<sms * 8, 256, 0, s>>>(n, W, rowat, posrow, nullptr, nullptr, X, out.status);
+  else if (m > 0)
+    gather_solution_kernel<<<sms * 8, 256, 0, s>>>(n, m, W + (size_t)n * n, rowat, nullptr, rhs->X, rhs->ldx,
+                                                   out.status);
   GJ_CUDA(cudaGetLastError());
   det_kernel<<<1, 1024, 0, s>>>(n, pivots, piv_rows, nullptr, out.status, out.det_sign, out.det_log2, out.fail_step);
   GJ_CUDA(cudaGetLastError());
@@ -959,9 +1015,13 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
 }
 
 gj_status run_unblocked(int64_t n64, const double* A, int64_t lda, double* X, int pivot_mode, double tau,
-                        const CtaOut& out, cudaStream_t s) {
+                        const CtaOut& out, cudaStream_t s, const Rhs* rhs) {
   if (n64 > 46340) return GJ_ERR_UNSUPPORTED;
   const int n = (int)n64;
+  const int64_t m = rhs ? rhs->m : 0;
+  if (n + m > 0x3fffffff) return GJ_ERR_UNSUPPORTED;
+  const int nw = (int)(n + m);
+  const bool solving = rhs != nullptr;
   WsList ws(s);
   double *W, *prow, *lcol, *pivots = out.pivots;
   int *posrow, *poscol, *rowat, *colat, *piv_rows = out.piv_rows, *piv_cols = out.piv_cols, *cand_k;
@@ -969,8 +1029,8 @@ gj_status run_unblocked(int64_t n64, const double* A, int64_t lda, double* X, in
   StepState* ss;
   const int sms = num_sms();
   const int G = sms * 4;
-  GJ_WS(W, (size_t)n * n);
-  GJ_WS(prow, (size_t)n);
+  GJ_WS(W, (size_t)n * nw);
+  GJ_WS(prow, (size_t)nw);
   GJ_WS(lcol, (size_t)n);
   GJ_WS(posrow, (size_t)n);
   GJ_WS(poscol, (size_t)n);
@@ -985,18 +1045,27 @@ gj_status run_unblocked(int64_t n64, const double* A, int64_t lda, double* X, in
 
   copy_in_kernel<<<sms * 8, 256, 0, s>>>(n, A, lda, W);
   GJ_CUDA(cudaGetLastError());
+  if (m > 0) {
+    copy_rhs_kernel<<<sms * 8, 256, 0, s>>>(n, m, rhs->B, rhs->ldb, W + (size_t)n * n);
+    GJ_CUDA(cudaGetLastError());
+  }
   init_positions_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, posrow, poscol, rowat, colat);
   GJ_CUDA(cudaGetLastError());
   scan0_kernel<<<G, 256, 0, s>>>(n, W, pivot_mode, cand_v, cand_k);
   GJ_CUDA(cudaGetLastError());
   prof_count(3 + 2 * n + 2);
   for (int k = 0; k < n; ++k) {
-    decide_kernel<<<1, 1024, 0, s>>>(n, k, G, cand_v, cand_k, W, rowat, colat, posrow, poscol, prow, lcol, ss, pivots,
-                                     piv_rows, piv_cols, out.status, out.fail_step, pivot_mode, tau);
-    rank1_kernel<<<G, 256, 0, s>>>(n, k, W, prow, lcol, ss, posrow, poscol, cand_v, cand_k, out.status, pivot_mode);
+    decide_kernel<<<1, 1024, 0, s>>>(n, nw, k, G, cand_v, cand_k, W, rowat, colat, posrow, poscol, prow, lcol, ss,
+                                     pivots, piv_rows, piv_cols, out.status, out.fail_step, pivot_mode, tau);
+    rank1_kernel<<<G, 256, 0, s>>>(n, nw, k, W, prow, lcol, ss, posrow, poscol, cand_v, cand_k, out.status,
+                                   pivot_mode);
   }
   GJ_CUDA(cudaGetLastError());
-  unpermute_kernel<<<sms * 8, 256, 0, s>>>(n, W, rowat, posrow, colat, poscol, X, out.status);
+  if (!solving)
+    unpermute_kernel<<<sms * 8, 256, 0, s>>>(n, W, rowat, posrow, colat, poscol, X, out.status);
+  else if (m > 0)
+    gather_solution_kernel<<<sms * 8, 256, 0, s>>>(n, m, W + (size_t)n * n, rowat, poscol, rhs->X, rhs->ldx,
+                                                   out.status);
   GJ_CUDA(cudaGetLastError());
   det_kernel<<<1, 1024, 0, s>>>(n, pivots, piv_rows, piv_cols, out.status, out.det_sign, out.det_log2,
                                 out.fail_step);

@@ -34,7 +34,7 @@ def lib():
 
 def test_header_declares_entry_points():
     names = _declared_functions()
-    for must in ("gj_invert", "gj_invert_ex", "gj_invert_batched", "gj_invert_batched_noalloc", "gj_batched_plan_create",
+    for must in ("gj_invert", "gj_invert_ex", "gj_solve", "gj_solve_ex", "gj_invert_batched", "gj_invert_batched_noalloc", "gj_batched_plan_create",
                  "gj_batched_plan_execute", "gj_batched_plan_destroy", "gj_status_string"):
         assert must in names
 
@@ -82,6 +82,21 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.gj_invert_mixed(4, p, 4, p, 3, 4, 0.0, 5, None, None, None, None, None, None) == gj.ERR_ARG
     assert L.gj_invert_mixed(4, p, 3, p, 3, 4, 1e-12, 5, None, None, None, None, None, None) == gj.ERR_ARG
     assert L.gj_invert_mixed(0, None, 1, None, 3, 4, 1e-12, 5, None, None, None, None, None, None) == gj.OK
+    # solve: negative sizes, leading dimensions below n, bad mode, null pointers, the
+    # single-CTA path (no right-hand sides there); n == 0 is the empty product
+    assert L.gj_solve(-1, 1, p, 1, p, 1, p, 1, 1, None, None) == gj.ERR_ARG
+    assert L.gj_solve(4, -1, p, 4, p, 4, p, 4, 1, None, None) == gj.ERR_ARG
+    assert L.gj_solve(4, 1, p, 3, p, 4, p, 4, 1, None, None) == gj.ERR_ARG
+    assert L.gj_solve(4, 1, p, 4, p, 3, p, 4, 1, None, None) == gj.ERR_ARG
+    assert L.gj_solve(4, 1, p, 4, p, 4, p, 3, 1, None, None) == gj.ERR_ARG
+    assert L.gj_solve(4, 1, p, 4, p, 4, p, 4, 7, None, None) == gj.ERR_ARG
+    assert L.gj_solve(4, 1, None, 4, p, 4, p, 4, 1, None, None) == gj.ERR_ARG
+    assert L.gj_solve(4, 2, p, 4, p, 4, p, 5, 1, None, None) == gj.ERR_ARG   # X == B with ldx != ldb
+    o = gj._Opts()
+    o.path = gj.PATH_CTA
+    assert L.gj_solve_ex(ctypes.byref(o), 4, 1, p, 4, p, 4, p, 4, 1, None, None) == gj.ERR_ARG
+    assert L.gj_solve(0, 3, None, 1, None, 1, None, 1, 1, ctypes.byref(sgn), ctypes.byref(lg)) == gj.OK
+    assert sgn.value == 1 and lg.value == 0.0
     plan = ctypes.c_void_p()
     nh = np.array([4, 200], dtype=np.int32)
     assert L.gj_batched_plan_create(ctypes.byref(plan), 2, nh.ctypes.data, 1) == gj.ERR_UNSUPPORTED
