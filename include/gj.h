@@ -240,6 +240,44 @@ typedef struct gj_plan gj_plan;
  */
 gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n_host, int pivot_mode);
 
+/* Kernel variants of a planned batch (one per order bin). */
+typedef enum {
+  GJ_BATCHED_WARP4 = 0,   /* one warp per matrix, 4 warps per CTA (orders <= 32, not full pivoting) */
+  GJ_BATCHED_WARP8 = 1,   /* one warp per matrix, 8 warps per CTA (same limits) */
+  GJ_BATCHED_CTA64 = 2,   /* one CTA of 64 threads per matrix, matrix in shared memory */
+  GJ_BATCHED_CTA128 = 3,  /* ... 128 threads */
+  GJ_BATCHED_CTA256 = 4,  /* ... 256 threads */
+  GJ_BATCHED_CTA512 = 5   /* ... 512 threads */
+} gj_batched_variant;
+
+/*
+ * gj_batched_plan_create_ex -- plan a batch with the kernel variant of each order bin
+ * (orders 0-8, 9-16, 17-24, 25-32, 33-48, 49-64, 65-96, 97-128) chosen by an autotuner.
+ * The paper has no counterpart (batching is outside its method).
+ *   tune_cache  host path of a text file (may be NULL): choices recorded there for this
+ *               device, pivot mode and bin are used first; new measurements are appended
+ *               (one line per bin: "gj-tune-v1 <device>_sm<SMs> <mode> <lo> <hi>
+ *               <variant> <microseconds>").  Within a process, measured choices are also
+ *               remembered in memory and reused by later plans.
+ *   variant     -1: autotune (time every applicable gj_batched_variant on up to 2048
+ *               synthetic matrices of the bin's orders, keep the fastest); otherwise that
+ *               variant for every bin it applies to (CTA128 / CTA256 elsewhere).
+ * Synchronous (it runs and times kernels on the legacy default stream while tuning).
+ * Other arguments and errors as for gj_batched_plan_create; GJ_ERR_ARG for a variant
+ * >= 6.
+ */
+gj_status gj_batched_plan_create_ex(gj_plan** plan, int64_t count, const int32_t* n_host, int pivot_mode,
+                                    const char* tune_cache, int32_t variant);
+
+/*
+ * gj_batched_plan_bins -- describe a plan's order bins (host arrays of max_bins entries,
+ * each may be NULL): orders lo..hi, number of matrices, chosen gj_batched_variant and the
+ * tuning time of that variant on the sample in microseconds (-1 when not measured in
+ * this call).  Returns the number of non-empty bins (0 for a NULL plan).
+ */
+int32_t gj_batched_plan_bins(const gj_plan* plan, int32_t* lo, int32_t* hi, int64_t* count, int32_t* variant,
+                             float* tuned_us, int32_t max_bins);
+
 /*
  * gj_batched_plan_execute -- run a planned batch on `stream`.  Argument meaning as in
  * gj_invert_batched (device arrays).  With use_graph != 0 the launch sequence is

@@ -23,6 +23,8 @@ OK, SINGULAR, ZERO_PIVOT, NONFINITE, NOT_CONVERGED = 0, 1, 2, 3, 4
 ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 PIVOT_NONE, PIVOT_PARTIAL, PIVOT_FULL = 0, 1, 2
 PATH_AUTO, PATH_CTA, PATH_BLOCKED, PATH_UNBLOCKED = 0, 1, 2, 3
+BATCHED_WARP4, BATCHED_WARP8, BATCHED_CTA64, BATCHED_CTA128, BATCHED_CTA256, BATCHED_CTA512 = range(6)
+BATCHED_NAMES = ["warp4", "warp8", "cta64", "cta128", "cta256", "cta512"]
 UPDATE_AUTO, UPDATE_DFMA, UPDATE_TC_OZAKI = 0, 1, 2
 
 
@@ -70,6 +72,10 @@ def lib() -> ctypes.CDLL:
     L.gj_invert_mixed.argtypes = [I64, P, I64, P, I, I, D, I, P, P, P, P, P, P]
     L.gj_batched_plan_create.restype = I
     L.gj_batched_plan_create.argtypes = [ctypes.POINTER(P), I64, P, I]
+    L.gj_batched_plan_create_ex.restype = I
+    L.gj_batched_plan_create_ex.argtypes = [ctypes.POINTER(P), I64, P, I, ctypes.c_char_p, I32]
+    L.gj_batched_plan_bins.restype = I32
+    L.gj_batched_plan_bins.argtypes = [P, P, P, P, P, P, I32]
     L.gj_batched_plan_execute.restype = I
     L.gj_batched_plan_execute.argtypes = [P, P, P, P, P, P, P, I]
     L.gj_batched_plan_destroy.restype = None
@@ -329,17 +335,36 @@ def invert_batched_noalloc(n_dev, A_ptrs, X_ptrs, status, det_sign=None, det_log
 
 
 class BatchedPlan:
-    """A planned batch (``gj_batched_plan_*``): fixed orders, largest-first order, graph replay."""
+    """A planned batch (``gj_batched_plan_*``): fixed orders, largest-first order, one
+    autotuned kernel variant per order bin, graph replay.
 
-    def __init__(self, n_host, pivot_mode: int = PIVOT_PARTIAL):
+    ``variant=-1`` autotunes (``BATCHED_*`` forces one variant); ``tune_cache`` is an
+    optional text file path for the tuner's choices."""
+
+    def __init__(self, n_host, pivot_mode: int = PIVOT_PARTIAL, *, variant: int = -1, tune_cache=None):
         import numpy as np
         L = lib()
         self._n = np.ascontiguousarray(n_host, dtype=np.int32)
         self.count = int(self._n.shape[0])
         self._plan = ctypes.c_void_p()
-        st = L.gj_batched_plan_create(ctypes.byref(self._plan), self.count, self._n.ctypes.data, int(pivot_mode))
+        cache = None if tune_cache is None else os.fsencode(tune_cache)
+        st = L.gj_batched_plan_create_ex(ctypes.byref(self._plan), self.count, self._n.ctypes.data, int(pivot_mode),
+                                         cache, int(variant))
         if st != OK:
-            raise GJError(st, "gj_batched_plan_create")
+            raise GJError(st, "gj_batched_plan_create_ex")
+
+    def bins(self) -> list[dict]:
+        """Order bins of the plan: ``lo``, ``hi``, ``count``, ``variant`` (name), ``tuned_us``."""
+        import numpy as np
+        lo = np.zeros(16, dtype=np.int32)
+        hi = np.zeros(16, dtype=np.int32)
+        cnt = np.zeros(16, dtype=np.int64)
+        var = np.zeros(16, dtype=np.int32)
+        us = np.zeros(16, dtype=np.float32)
+        nb = lib().gj_batched_plan_bins(self._plan, lo.ctypes.data, hi.ctypes.data, cnt.ctypes.data, var.ctypes.data,
+                                        us.ctypes.data, 16)
+        return [{"lo": int(lo[b]), "hi": int(hi[b]), "count": int(cnt[b]), "variant": BATCHED_NAMES[int(var[b])],
+                 "tuned_us": float(us[b])} for b in range(nb)]
 
     def execute(self, A_ptrs, X_ptrs, status, det_sign=None, det_log2=None, *, stream=None,
                 use_graph: bool = True) -> None:

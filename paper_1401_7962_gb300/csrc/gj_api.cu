@@ -4,7 +4,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "gj_internal.cuh"
@@ -374,6 +378,171 @@ gj_status gj_invert_batched(int64_t count, int32_t nmax, const int32_t* n, const
 }  // extern "C"
 
 // ------------------------------------------------------------------ batched plans
+//
+// A plan fixes the orders of a batch.  It sorts the work largest order first, splits it
+// into order bins, and picks for every bin the kernel variant (one warp per matrix, or one
+// CTA of 64 / 128 / 256 / 512 threads per matrix) that runs fastest on this GPU: the
+// autotuner times each applicable variant on synthetic matrices of the bin's orders and
+// keeps the best, remembering the choice per device, pivot mode and bin (in memory, and
+// in an optional text cache file).  Executing the plan launches one persistent kernel per
+// bin; with use_graph the launches are captured once and replayed as a CUDA graph.
+
+namespace gj {
+namespace {
+
+constexpr int kBinEdges[] = {0, 8, 16, 24, 32, 48, 64, 96, 128};  // bin b holds orders (edge[b], edge[b+1]]
+constexpr int kNumBins = 8;
+
+struct PlanBin {
+  int lo = 0, hi = 0;             // orders lo..hi (inclusive)
+  int64_t q_begin = 0, q_end = 0;  // range of the work order
+  int nmax = 0;                    // largest order present
+  int variant = kVarCta128;
+  float tuned_us = -1.0f;          // time of the chosen variant on the tuning sample
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<std::string, int, int, int>, std::pair<int, float>> g_tune_memo;
+
+std::string device_tag() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name(prop.name);
+  for (char& ch : name)
+    if (ch == ' ') ch = '_';
+  return name + "_sm" + std::to_string(prop.multiProcessorCount);
+}
+
+// Diagonally dominant test matrices for timing (values from a hash of the index).
+__global__ void tune_fill_kernel(int64_t count, const int32_t* __restrict__ nv, const int64_t* __restrict__ off,
+                                 double* __restrict__ data) {
+  for (int64_t m = blockIdx.x; m < count; m += gridDim.x) {
+    const int n = nv[m];
+    double* A = data + off[m];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int j = e / n, i = e - j * n;
+      uint32_t h = (uint32_t)(m * 2654435761u) ^ (uint32_t)(e * 40503u + 12345u);
+      h ^= h >> 13;
+      h *= 0x5bd1e995u;
+      h ^= h >> 15;
+      const double v = ((double)(h & 0xffffff) / 16777216.0) * 2.0 - 1.0;
+      A[e] = (i == j) ? (double)n + 1.0 + v : v;
+    }
+  }
+}
+
+__global__ void tune_ptrs_kernel(int64_t count, const int64_t* __restrict__ off, double* base_a, double* base_x,
+                                 const double** pa, double** px) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < count; m += (int64_t)gridDim.x * blockDim.x) {
+    pa[m] = base_a + off[m];
+    px[m] = base_x + off[m];
+  }
+}
+
+bool read_tune_cache(const char* path, const std::string& tag, int mode, int lo, int hi, int* variant) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    char t[256];
+    int md, l, h, v;
+    if (sscanf(line, "gj-tune-v1 %255s %d %d %d %d", t, &md, &l, &h, &v) == 5 && tag == t && md == mode &&
+        l == lo && h == hi && v >= 0 && v < kNumVariants) {
+      *variant = v;  // the last matching line wins
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void append_tune_cache(const char* path, const std::string& tag, int mode, int lo, int hi, int variant, float us) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "gj-tune-v1 %s %d %d %d %d %.3f\n", tag.c_str(), mode, lo, hi, variant, us);
+  fclose(f);
+}
+
+// Time every applicable variant on up to 2048 matrices spread over the bin's orders.
+gj_status autotune_bin(const std::vector<int32_t>& sorted_n, PlanBin& b, int mode, int* best, float* best_us) {
+  const int64_t cnt = b.q_end - b.q_begin;
+  const int64_t sample = std::min<int64_t>(cnt, 2048);
+  std::vector<int32_t> ns((size_t)sample);
+  std::vector<int64_t> off((size_t)sample);
+  int64_t total = 0;
+  for (int64_t t = 0; t < sample; ++t) {
+    ns[t] = sorted_n[(size_t)(b.q_begin + (t * cnt) / sample)];
+    off[t] = total;
+    total += (int64_t)ns[t] * ns[t];
+  }
+  int32_t *d_n = nullptr, *d_status = nullptr, *d_counter = nullptr;
+  int64_t* d_off = nullptr;
+  double *d_a = nullptr, *d_x = nullptr;
+  const double** d_pa = nullptr;
+  double** d_px = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  gj_status st = GJ_OK;
+  auto fail = [&](cudaError_t e, const char* what) {
+    st = cuda_fail(e, what);
+    return st;
+  };
+  do {
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_n, sizeof(int32_t) * sample)) != cudaSuccess) { fail(e, "autotune"); break; }
+    if ((e = cudaMalloc(&d_status, sizeof(int32_t) * sample)) != cudaSuccess) { fail(e, "autotune"); break; }
+    if ((e = cudaMalloc(&d_counter, sizeof(int32_t))) != cudaSuccess) { fail(e, "autotune"); break; }
+    if ((e = cudaMalloc(&d_off, sizeof(int64_t) * sample)) != cudaSuccess) { fail(e, "autotune"); break; }
+    if ((e = cudaMalloc(&d_a, sizeof(double) * std::max<int64_t>(total, 1))) != cudaSuccess) { fail(e, "autotune"); break; }
+    if ((e = cudaMalloc(&d_x, sizeof(double) * std::max<int64_t>(total, 1))) != cudaSuccess) { fail(e, "autotune"); break; }
+    if ((e = cudaMalloc(&d_pa, sizeof(double*) * sample)) != cudaSuccess) { fail(e, "autotune"); break; }
+    if ((e = cudaMalloc(&d_px, sizeof(double*) * sample)) != cudaSuccess) { fail(e, "autotune"); break; }
+    cudaMemcpy(d_n, ns.data(), sizeof(int32_t) * sample, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_off, off.data(), sizeof(int64_t) * sample, cudaMemcpyHostToDevice);
+    tune_fill_kernel<<<256, 256>>>(sample, d_n, d_off, d_a);
+    tune_ptrs_kernel<<<64, 256>>>(sample, d_off, d_a, d_x, d_pa, d_px);
+    if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "autotune"); break; }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    CtaOut out{};
+    out.status = d_status;
+    *best = -1;
+    *best_us = 0.0f;
+    for (int v = 0; v < kNumVariants && st == GJ_OK; ++v) {
+      if (!batched_variant_applies(v, b.nmax, mode)) continue;
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {  // first run warms up
+        cudaMemsetAsync(d_counter, 0, sizeof(int32_t), 0);
+        cudaEventRecord(e0, 0);
+        gj_status ls = launch_batched_variant(v, 0, sample, b.nmax, d_n, d_pa, d_px, nullptr, d_counter, mode, 0.0,
+                                              out, 0);
+        cudaEventRecord(e1, 0);
+        if (ls != GJ_OK) { st = ls; break; }
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { fail(e, "autotune"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) t_min = std::min(t_min, ms * 1000.0f);
+      }
+      if (st == GJ_OK && (*best < 0 || t_min < *best_us)) {
+        *best = v;
+        *best_us = t_min;
+      }
+    }
+  } while (false);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  void* ps[] = {d_n, d_status, d_counter, d_off, d_a, d_x, (void*)d_pa, (void*)d_px};
+  for (void* q : ps)
+    if (q) cudaFree(q);
+  return st;
+}
+
+}  // namespace
+}  // namespace gj
 
 struct gj_plan {
   int64_t count = 0;
@@ -383,7 +552,8 @@ struct gj_plan {
   int pivot_mode = 1;
   int32_t* d_n = nullptr;
   int32_t* d_order = nullptr;
-  int32_t* d_counter = nullptr;
+  int32_t* d_counter = nullptr;  // one counter per bin
+  std::vector<PlanBin> bins;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -391,23 +561,29 @@ struct gj_plan {
 
 static gj_status plan_enqueue(gj_plan* p, const double* const* A, double* const* Ainv, int32_t* status,
                               int8_t* det_sign, double* det_log2, cudaStream_t s) {
-  GJ_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int32_t), s));
+  GJ_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(int32_t) * kNumBins, s));
   CtaOut out{};
   out.status = status;
   out.det_sign = det_sign;
   out.det_log2 = det_log2;
-  return launch_cta_batched(p->count, p->nmax, p->d_n, A, Ainv, p->d_order, p->d_counter, p->pivot_mode, 0.0, out,
-                            s);
+  for (size_t b = 0; b < p->bins.size(); ++b) {
+    const PlanBin& pb = p->bins[b];
+    GJ_TRY(launch_batched_variant(pb.variant, pb.q_begin, pb.q_end, pb.nmax, p->d_n, A, Ainv, p->d_order,
+                                  p->d_counter + b, p->pivot_mode, 0.0, out, s));
+  }
+  return GJ_OK;
 }
 
 extern "C" {
 
-gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n_host, int pivot_mode) {
+gj_status gj_batched_plan_create_ex(gj_plan** plan, int64_t count, const int32_t* n_host, int pivot_mode,
+                                    const char* tune_cache, int32_t variant) {
   g_last_error[0] = '\0';
   if (!plan) return GJ_ERR_ARG;
   *plan = nullptr;
   if (count < 0 || count > 0x7fffffffLL || (count > 0 && !n_host)) return GJ_ERR_ARG;
   if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
+  if (variant >= kNumVariants) return GJ_ERR_ARG;
   int nmax = 1;
   for (int64_t m = 0; m < count; ++m) {
     if (n_host[m] < 0 || n_host[m] > kCtaMaxN) return GJ_ERR_UNSUPPORTED;
@@ -417,18 +593,33 @@ gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n
   p->count = count;
   p->nmax = nmax;
   p->pivot_mode = pivot_mode;
-  // largest order first (longest-processing-time order for the persistent queue)
+  // largest order first (longest-processing-time order for the persistent queues)
   std::vector<int32_t> order((size_t)count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return n_host[a] > n_host[b]; });
+  std::vector<int32_t> sorted_n((size_t)count);
+  for (int64_t q = 0; q < count; ++q) sorted_n[q] = n_host[order[q]];
   for (int64_t m = 0; m < count; ++m) {
     const double nm = (double)n_host[m];
     p->flops += 2.0 * nm * nm * nm;
     p->bytes += 16.0 * nm * nm;
   }
+  // order bins: contiguous ranges of the descending work order
+  for (int b = kNumBins - 1; b >= 0; --b) {
+    PlanBin pb;
+    pb.lo = (b == 0) ? 0 : kBinEdges[b] + 1;
+    pb.hi = kBinEdges[b + 1];
+    const auto first = std::lower_bound(sorted_n.begin(), sorted_n.end(), pb.hi, std::greater<int32_t>());
+    const auto last = std::upper_bound(sorted_n.begin(), sorted_n.end(), pb.lo, std::greater<int32_t>());
+    pb.q_begin = first - sorted_n.begin();
+    pb.q_end = last - sorted_n.begin();
+    if (pb.q_end <= pb.q_begin) continue;
+    pb.nmax = std::max(1, (int)sorted_n[pb.q_begin]);
+    p->bins.push_back(pb);
+  }
   cudaError_t e = cudaMalloc(&p->d_n, sizeof(int32_t) * (count > 0 ? count : 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int32_t) * (count > 0 ? count : 1));
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(int32_t) * kNumBins);
   if (e == cudaSuccess && count > 0) e = cudaMemcpy(p->d_n, n_host, sizeof(int32_t) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && count > 0)
     e = cudaMemcpy(p->d_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
@@ -436,8 +627,65 @@ gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n
     gj_batched_plan_destroy(p);
     return cuda_fail(e, "gj_batched_plan_create");
   }
+  // kernel variant per bin: forced, cached, or measured
+  const std::string tag = device_tag();
+  for (PlanBin& pb : p->bins) {
+    const int fallback = (pb.nmax > 64) ? kVarCta256 : kVarCta128;
+    if (variant >= 0) {
+      pb.variant = batched_variant_applies(variant, pb.nmax, pivot_mode) ? variant : fallback;
+      continue;
+    }
+    const auto key = std::make_tuple(tag, pivot_mode, pb.lo, pb.hi);
+    int v = -1;
+    // the caller's cache file first, then this process's earlier measurements
+    if (read_tune_cache(tune_cache, tag, pivot_mode, pb.lo, pb.hi, &v) &&
+        batched_variant_applies(v, pb.nmax, pivot_mode)) {
+      pb.variant = v;
+      continue;
+    }
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_memo.find(key);
+      if (it != g_tune_memo.end() && batched_variant_applies(it->second.first, pb.nmax, pivot_mode)) {
+        pb.variant = it->second.first;
+        continue;
+      }
+    }
+    float us = 0.0f;
+    gj_status st = autotune_bin(sorted_n, pb, pivot_mode, &v, &us);
+    if (st != GJ_OK || v < 0) {
+      gj_batched_plan_destroy(p);
+      return st != GJ_OK ? st : GJ_ERR_UNSUPPORTED;
+    }
+    pb.variant = v;
+    pb.tuned_us = us;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_memo[key] = {v, us};
+    }
+    append_tune_cache(tune_cache, tag, pivot_mode, pb.lo, pb.hi, v, us);
+  }
   *plan = p;
   return GJ_OK;
+}
+
+gj_status gj_batched_plan_create(gj_plan** plan, int64_t count, const int32_t* n_host, int pivot_mode) {
+  return gj_batched_plan_create_ex(plan, count, n_host, pivot_mode, nullptr, -1);
+}
+
+int32_t gj_batched_plan_bins(const gj_plan* p, int32_t* lo, int32_t* hi, int64_t* count, int32_t* variant,
+                             float* tuned_us, int32_t max_bins) {
+  if (!p) return 0;
+  const int32_t nb = (int32_t)p->bins.size();
+  for (int32_t b = 0; b < nb && b < max_bins; ++b) {
+    const PlanBin& pb = p->bins[b];
+    if (lo) lo[b] = pb.lo;
+    if (hi) hi[b] = pb.hi;
+    if (count) count[b] = pb.q_end - pb.q_begin;
+    if (variant) variant[b] = pb.variant;
+    if (tuned_us) tuned_us[b] = pb.tuned_us;
+  }
+  return nb;
 }
 
 gj_status gj_batched_plan_execute(gj_plan* p, const double* const* A, double* const* Ainv, int32_t* status,
@@ -481,7 +729,7 @@ gj_status gj_batched_plan_execute(gj_plan* p, const double* const* A, double* co
     for (int i = 0; i < 6; ++i) p->key[i] = key[i];
   }
   {
-    ProfScope ps(s, "cta_batched", p->flops, p->bytes);
+    ProfScope ps(s, "batched_plan", p->flops, p->bytes);
     GJ_CUDA(cudaGraphLaunch(p->exec, s));
   }
   prof_count(1);

@@ -104,6 +104,16 @@ gj_status launch_cta_batched(int64_t count, int nmax, const int32_t* n, const do
                              double tau, const CtaOut& out, cudaStream_t s);
 
 // Device-side work order: counting sort of the orders, largest first.  Writes
+// Kernel variants of the batched inversion, chosen per order bin by the plan's autotuner:
+// one warp per matrix (orders <= 32, partial / no pivoting; 4 or 8 warps per CTA) or one
+// CTA of NT threads per matrix in shared memory.
+enum BatchedVariant { kVarWarp4 = 0, kVarWarp8, kVarCta64, kVarCta128, kVarCta256, kVarCta512, kNumVariants };
+bool batched_variant_applies(int variant, int nmax, int pivot_mode);
+// Items q_begin .. q_end - 1 of `order` with one kernel variant; *counter must be 0.
+gj_status launch_batched_variant(int variant, int64_t q_begin, int64_t q_end, int nmax, const int32_t* n,
+                                 const double* const* A, double* const* X, const int32_t* order, int32_t* counter,
+                                 int pivot_mode, double tau, const CtaOut& out, cudaStream_t s);
+
 // order[count]; ws must hold (kCtaMaxN + 2) int32.  Also leaves *counter = 0.
 gj_status launch_order_by_size(int64_t count, const int32_t* n, int32_t* order, int32_t* ws, int32_t* counter,
                                cudaStream_t s);

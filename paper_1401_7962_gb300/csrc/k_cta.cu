@@ -284,8 +284,11 @@ __global__ void __launch_bounds__(NT) cta_single_kernel(int n, const double* A, 
   solve_matrix<NT>(n, A, lda, X, mode, tau, out, 0, true, smem, n);
 }
 
+// Persistent: the CTA takes work items q_begin, q_begin + 1, ... < q_end from a shared
+// counter; item q is matrix order[q] (the work order lists the largest orders first).
 template <int NT>
-__global__ void __launch_bounds__(NT) cta_batched_kernel(int64_t count, int nmax, const int32_t* __restrict__ nv,
+__global__ void __launch_bounds__(NT) cta_batched_kernel(int64_t q_begin, int64_t q_end, int nmax,
+                                                         const int32_t* __restrict__ nv,
                                                          const double* const* __restrict__ A,
                                                          double* const* __restrict__ X,
                                                          const int32_t* __restrict__ order, int32_t* counter,
@@ -295,9 +298,9 @@ __global__ void __launch_bounds__(NT) cta_batched_kernel(int64_t count, int nmax
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
-    const int64_t q = s_item;
+    const int64_t q = q_begin + s_item;
     __syncthreads();
-    if (q >= count) break;
+    if (q >= q_end) break;
     const int64_t m = order ? order[q] : q;
     const int n = nv[m];
     if (n < 0 || n > nmax) {
@@ -311,6 +314,114 @@ __global__ void __launch_bounds__(NT) cta_batched_kernel(int64_t count, int nmax
     }
     solve_matrix<NT>(n, A[m], n > 0 ? n : 1, X[m], mode, tau, out, m, false, smem, nmax);
     __syncthreads();
+  }
+}
+
+// One warp inverts one matrix of order n <= 32 held in registers: lane i keeps row i of
+// the compact [A | D] array (w[j] = W[i, j]).  Interchanges stay implicit (each lane
+// knows the position of its row); per step the candidates of eq. 14 are compared across
+// the warp by shuffles, the pivot row is broadcast from its lane by shuffles and every
+// lane applies eq. 15 to its own row.  No shared memory, no block barriers.  Partial or
+// no pivoting (full pivoting needs column positions in every lane: the CTA kernel).
+template <int WPC>
+__global__ void __launch_bounds__(WPC * 32) warp_batched_kernel(int64_t q_begin, int64_t q_end,
+                                                                const int32_t* __restrict__ nv,
+                                                                const double* const* __restrict__ A,
+                                                                double* const* __restrict__ X,
+                                                                const int32_t* __restrict__ order,
+                                                                int32_t* counter, int mode, double tau,
+                                                                CtaOut out) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    const int64_t q = q_begin + __shfl_sync(0xffffffffu, item, 0);
+    if (q >= q_end) break;
+    const int64_t m = order ? order[q] : q;
+    const int n = nv[m];
+    if (n < 0 || n > 32) {
+      if (lane == 0) {
+        if (out.status) out.status[m] = GJ_ERR_ARG;
+        if (out.det_sign) out.det_sign[m] = 0;
+        if (out.det_log2) out.det_log2[m] = -INFINITY;
+        if (out.fail_step) out.fail_step[m] = -1;
+      }
+      continue;
+    }
+    const double* __restrict__ Am = A[m];
+    double w[32];
+    const bool live = lane < n;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) w[j] = (live && j < n) ? Am[lane + j * n] : 0.0;
+    int pos = lane;       // position of this lane's row (rows of lanes >= n are never candidates)
+    bool used = !live;    // row already chosen as a pivot row
+    int sign = 1, status = GJ_OK, fail = -1;
+    double lg = 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k >= n) break;
+      // ---- pivot candidates of step k (observations 2-3), compared on the integer pipe
+      uint64_t bv = 0;
+      int bk = kNoKey;
+      if (mode == GJ_PIVOT_NONE) {
+        if (live && pos == k) {
+          bv = abs_bits(w[k]);
+          bk = k;
+        }
+      } else if (!used) {
+        bv = abs_bits(w[k]);
+        bk = pos;
+      }
+      warp_argmax(bv, bk);
+      if (bk == kNoKey || __longlong_as_double((long long)bv) <= tau) {
+        status = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+        fail = k;
+        break;
+      }
+      if (bv >= kInfBits) {
+        status = GJ_NONFINITE;
+        fail = k;
+        break;
+      }
+      const int rp = bk;  // position of the pivot row
+      const int R = __ffs(__ballot_sync(0xffffffffu, live && pos == rp)) - 1;
+      if (rp != k) {
+        sign = -sign;
+        pos = (pos == k) ? rp : (pos == rp ? k : pos);
+      }
+      const double qv = __shfl_sync(0xffffffffu, w[k], R);
+      if (qv < 0.0) sign = -sign;
+      lg += log2(fabs(qv));
+      const double inv_q = 1.0 / qv;
+      // ---- eq. 14 (pivot row, broadcast) and eq. 15 (own row); the slot of column k
+      //      carries D's column from now on
+      const bool isR = lane == R;
+      const double l = w[k];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j >= n) break;
+        const double pj = (j == k) ? inv_q : __shfl_sync(0xffffffffu, w[j], R) * inv_q;
+        w[j] = isR ? pj : fma(-l, pj, (j == k) ? 0.0 : w[j]);
+      }
+      if (isR) used = true;
+    }
+    if (status == GJ_OK) {
+      // reverse-order un-permutation (observation 3) as one gather: the row of position p
+      // goes to output row p, column c of W to output column rowat[c]
+      double* __restrict__ Xm = X[m];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c >= n) break;
+        const int col = __ffs(__ballot_sync(0xffffffffu, live && pos == c)) - 1;
+        if (live) Xm[pos + col * n] = w[c];
+      }
+    }
+    if (lane == 0) {
+      if (out.status) out.status[m] = status;
+      if (out.det_sign) out.det_sign[m] = (int8_t)(status == GJ_OK ? sign : 0);
+      if (out.det_log2) out.det_log2[m] = (status == GJ_OK) ? lg : -INFINITY;
+      if (out.fail_step) out.fail_step[m] = (status == GJ_OK) ? -1 : fail;
+    }
   }
 }
 
@@ -344,9 +455,9 @@ __global__ void order_scatter_kernel(int64_t count, const int32_t* __restrict__ 
 }
 
 template <int NT>
-gj_status launch_batched_nt(int64_t count, int nmax, const int32_t* n, const double* const* A, double* const* X,
-                            const int32_t* order, int32_t* counter, int mode, double tau, const CtaOut& out,
-                            cudaStream_t s) {
+gj_status launch_batched_nt(int64_t q_begin, int64_t q_end, int nmax, const int32_t* n, const double* const* A,
+                            double* const* X, const int32_t* order, int32_t* counter, int mode, double tau,
+                            const CtaOut& out, cudaStream_t s) {
   const size_t smem = cta_smem_bytes(nmax);
   auto kern = cta_batched_kernel<NT>;
   GJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -356,11 +467,32 @@ gj_status launch_batched_nt(int64_t count, int nmax, const int32_t* n, const dou
   GJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
   if (per_sm < 1) return GJ_ERR_UNSUPPORTED;
   int64_t grid = (int64_t)sms * per_sm;
-  if (grid > count) grid = count;
+  if (grid > q_end - q_begin) grid = q_end - q_begin;
   if (grid < 1) grid = 1;
   prof_count(1);
   ProfScope ps(s, "cta_batched", 0.0, 0.0);
-  kern<<<(unsigned)grid, NT, smem, s>>>(count, nmax, n, A, X, order, counter, mode, tau, out);
+  kern<<<(unsigned)grid, NT, smem, s>>>(q_begin, q_end, nmax, n, A, X, order, counter, mode, tau, out);
+  GJ_CUDA(cudaGetLastError());
+  return GJ_OK;
+}
+
+template <int WPC>
+gj_status launch_batched_warp(int64_t q_begin, int64_t q_end, const int32_t* n, const double* const* A,
+                              double* const* X, const int32_t* order, int32_t* counter, int mode, double tau,
+                              const CtaOut& out, cudaStream_t s) {
+  auto kern = warp_batched_kernel<WPC>;
+  int dev = 0, sms = 0, per_sm = 0;
+  GJ_CUDA(cudaGetDevice(&dev));
+  GJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPC * 32, 0));
+  if (per_sm < 1) return GJ_ERR_UNSUPPORTED;
+  int64_t grid = (int64_t)sms * per_sm;
+  const int64_t need = (q_end - q_begin + WPC - 1) / WPC;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  prof_count(1);
+  ProfScope ps(s, "warp_batched", 0.0, 0.0);
+  kern<<<(unsigned)grid, WPC * 32, 0, s>>>(q_begin, q_end, n, A, X, order, counter, mode, tau, out);
   GJ_CUDA(cudaGetLastError());
   return GJ_OK;
 }
@@ -395,9 +527,46 @@ gj_status launch_cta_batched(int64_t count, int nmax, const int32_t* n, const do
   if (count <= 0) return GJ_OK;
   if (nmax < 1) nmax = 1;
   if (nmax > kCtaMaxN) return GJ_ERR_ARG;
-  if (nmax > 64) return launch_batched_nt<256>(count, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
-  if (nmax > 16) return launch_batched_nt<128>(count, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
-  return launch_batched_nt<64>(count, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+  if (nmax > 64) return launch_batched_nt<256>(0, count, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+  if (nmax > 16) return launch_batched_nt<128>(0, count, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+  return launch_batched_nt<64>(0, count, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+}
+
+bool batched_variant_applies(int variant, int nmax, int pivot_mode) {
+  switch (variant) {
+    case kVarWarp4:
+    case kVarWarp8:
+      return nmax <= 32 && pivot_mode != GJ_PIVOT_FULL;
+    case kVarCta64:
+    case kVarCta128:
+    case kVarCta256:
+    case kVarCta512:
+      return nmax <= kCtaMaxN;
+    default:
+      return false;
+  }
+}
+
+gj_status launch_batched_variant(int variant, int64_t q_begin, int64_t q_end, int nmax, const int32_t* n,
+                                 const double* const* A, double* const* X, const int32_t* order, int32_t* counter,
+                                 int pivot_mode, double tau, const CtaOut& out, cudaStream_t s) {
+  if (q_end <= q_begin) return GJ_OK;
+  if (nmax < 1) nmax = 1;
+  if (!batched_variant_applies(variant, nmax, pivot_mode)) return GJ_ERR_ARG;
+  switch (variant) {
+    case kVarWarp4:
+      return launch_batched_warp<4>(q_begin, q_end, n, A, X, order, counter, pivot_mode, tau, out, s);
+    case kVarWarp8:
+      return launch_batched_warp<8>(q_begin, q_end, n, A, X, order, counter, pivot_mode, tau, out, s);
+    case kVarCta64:
+      return launch_batched_nt<64>(q_begin, q_end, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+    case kVarCta128:
+      return launch_batched_nt<128>(q_begin, q_end, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+    case kVarCta256:
+      return launch_batched_nt<256>(q_begin, q_end, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+    default:
+      return launch_batched_nt<512>(q_begin, q_end, nmax, n, A, X, order, counter, pivot_mode, tau, out, s);
+  }
 }
 
 gj_status launch_order_by_size(int64_t count, const int32_t* n, int32_t* order, int32_t* ws, int32_t* counter,

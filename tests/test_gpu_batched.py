@@ -123,3 +123,76 @@ def test_batched_200k_workload_sampled():
     idx = rng.choice(len(sizes), 300, replace=False)
     compare(sizes, packed, offsets, dX.cpu().numpy(), stc, sgc, lg.cpu().numpy(), idx)
     plan.close()
+
+
+def _gaussian_batch(count, seed, n_lo, n_hi):
+    """Orders uniform in n_lo..n_hi, N(0,1) entries (needs pivoting); n = 0 included when n_lo = 0."""
+    g = wl.rng(seed)
+    sizes = g.integers(n_lo, n_hi + 1, size=count).astype(np.int32)
+    sq = sizes.astype(np.int64) ** 2
+    offsets = np.zeros(count, dtype=np.int64)
+    offsets[1:] = np.cumsum(sq)[:-1]
+    packed = g.standard_normal(int(sq.sum()))
+    return sizes, packed, offsets
+
+
+@pytest.mark.parametrize("variant", [gj.BATCHED_WARP4, gj.BATCHED_WARP8])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plan_warp_variants_match_oracle(variant, mode):
+    """One warp per matrix (orders <= 32): every matrix of a mixed batch against the oracle,
+    including order 0 and 1, and pivoting inputs (N(0,1) entries) for partial pivoting."""
+    if mode == 0:  # no pivoting: diagonally dominant inputs
+        sizes, packed, offsets = wl.diag_dominant_batch(500, seed=310 + variant, n_min=1, n_max=32)
+    else:
+        sizes, packed, offsets = _gaussian_batch(500, 320 + variant, 0, 32)
+    plan = gj.BatchedPlan(sizes, mode, variant=variant)
+    bins = plan.bins()
+    assert all(b["variant"] == gj.BATCHED_NAMES[variant] for b in bins)
+    dA, dX, ap, xp, nd, st, sg, lg = to_device_batch(sizes, packed, offsets)
+    plan.execute(ap, xp, st, sg, lg, use_graph=False)
+    torch.cuda.synchronize()
+    compare(sizes, packed, offsets, dX.cpu().numpy(), st.cpu().numpy(), sg.cpu().numpy(), lg.cpu().numpy(),
+            range(len(sizes)), mode=mode)
+
+
+@pytest.mark.parametrize("variant", [gj.BATCHED_CTA64, gj.BATCHED_CTA128, gj.BATCHED_CTA256, gj.BATCHED_CTA512])
+def test_plan_cta_variants_match_oracle(variant):
+    sizes, packed, offsets = _gaussian_batch(300, 330 + variant, 1, 128)
+    for mode in (1, 2):
+        plan = gj.BatchedPlan(sizes, mode, variant=variant)
+        dA, dX, ap, xp, nd, st, sg, lg = to_device_batch(sizes, packed, offsets)
+        plan.execute(ap, xp, st, sg, lg)
+        torch.cuda.synchronize()
+        compare(sizes, packed, offsets, dX.cpu().numpy(), st.cpu().numpy(), sg.cpu().numpy(), lg.cpu().numpy(),
+                range(0, len(sizes), 3), mode=mode)
+
+
+def test_plan_autotuner_choices_and_cache(tmp_path):
+    """The autotuned plan: every bin gets an applicable variant, results match the oracle,
+    measured choices are written to the cache file, and a cache entry is honoured."""
+    sizes, packed, offsets = _gaussian_batch(3000, 340, 1, 128)
+    cache = tmp_path / "tune.txt"
+    plan = gj.BatchedPlan(sizes, 1, tune_cache=str(cache))
+    bins = plan.bins()
+    assert sum(b["count"] for b in bins) == len(sizes)
+    lines = cache.read_text().splitlines() if cache.exists() else []
+    for b in bins:
+        assert b["variant"] in gj.BATCHED_NAMES
+        if b["hi"] > 32:
+            assert b["variant"].startswith("cta")
+        if b["tuned_us"] >= 0:  # measured now: recorded in the cache
+            assert any(ln.split()[3:6] == [str(b["lo"]), str(b["hi"]), str(gj.BATCHED_NAMES.index(b["variant"]))]
+                       for ln in lines), (b, lines)
+    dA, dX, ap, xp, nd, st, sg, lg = to_device_batch(sizes, packed, offsets)
+    plan.execute(ap, xp, st, sg, lg)
+    torch.cuda.synchronize()
+    compare(sizes, packed, offsets, dX.cpu().numpy(), st.cpu().numpy(), sg.cpu().numpy(), lg.cpu().numpy(),
+            range(0, len(sizes), 25), mode=1)
+    # a cache entry is used as written (here: 64-thread CTAs for orders 33..48)
+    props = torch.cuda.get_device_properties(0)
+    tag = props.name.replace(" ", "_") + "_sm" + str(props.multi_processor_count)
+    forced = tmp_path / "forced.txt"
+    forced.write_text(f"gj-tune-v1 {tag} 1 33 48 {gj.BATCHED_CTA64} 1.0\n")
+    plan2 = gj.BatchedPlan(sizes, 1, tune_cache=str(forced))
+    b33 = [b for b in plan2.bins() if b["lo"] == 33]
+    assert b33 and b33[0]["variant"] == "cta64" and b33[0]["tuned_us"] < 0

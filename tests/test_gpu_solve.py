@@ -175,4 +175,5 @@ def test_solve_8192_workload_properties():
     assert res <= n * 1e-15, res  # the gate of the smaller cases (n x 4.5 eps)
     ref = np.linalg.solve(A, B)
     Xh = X.cpu().numpy()
-    assert np.max(np.abs(Xh - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # kappa_2(A) <= (0.1 n + 2 sqrt(n)) / (0.1 n - 2 sqrt(n)) < 2 for N(0,1) + 0.1 n I at this n
+    assert np.max(np.abs(Xh - ref)) <= 64 * n * 2.0 * EPS * np.max(np.abs(ref))
