@@ -43,12 +43,17 @@ constexpr int kTM = 128;          // tile rows (MMA M)
 constexpr int kTN = 64;           // tile columns (MMA N)
 constexpr int kKB = 128;          // slice row length in elements (max inner dimension)
 constexpr int kKC = 64;           // elements per TMA box along k (128 bytes, one swizzle row)
-constexpr int kStages = 4;        // ring of L-slice boxes (16 KiB each)
-constexpr int kABox = kTM * kKC * 2;   // 16 KiB
+constexpr int kStages = 2;        // ring of L slices: one stage = one digit slice, kKB wide
+constexpr int kABox = kTM * kKC * 2;   // 16 KiB: one TMA box (128 rows x 64 k)
+constexpr int kAStage = 2 * kABox;     // 32 KiB: the two boxes of a slice (k 0..63, 64..127)
 constexpr int kBBox = kTN * kKC * 2;   // 8 KiB
-constexpr int kEpiWarps = 8;      // two per TMEM lane quarter, each taking half of the tile's columns
+#ifndef GJ_EPI_WARPS
+#define GJ_EPI_WARPS 8
+#endif
+constexpr int kEpiWarps = GJ_EPI_WARPS;  // per TMEM lane quarter kEpiWarps / 4, each with a column slice
+constexpr int kEpiSlices = kEpiWarps / 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
-constexpr int kEpiCols = kTN / 2;  // columns per epilogue thread
+constexpr int kEpiCols = kTN / kEpiSlices;  // columns per epilogue thread
 constexpr int kCSm = kEpiCols / 2; // of those, prefetched into shared memory (the rest load in the final pass)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
@@ -190,9 +195,20 @@ __device__ __forceinline__ double i64_times_pow2(long long T, int e) {
 }
 
 
+// T * 2^e via the hardware conversion of T (correctly rounded) and an exponent add (exact
+// for normal results; the same value as i64_times_pow2, and faster in the epilogue).
+__device__ __forceinline__ double i64_to_double_pow2(long long T, int e) {
+  const double d = __ll2double_rn(T);
+  const long long bits = __double_as_longlong(d);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (d == 0.0 || E + e <= 0 || E + e >= 2047) return ldexp(d, e);
+  return __longlong_as_double(bits + (static_cast<long long>(e) << 52));
+}
+
 struct SmemLayout {
   static size_t bytes(int S) {
-    return 1024 /*align slack*/ + (size_t)S * 2 * kBBox + (size_t)kStages * kABox + (size_t)2 * kCSm * kTM * 8;
+    return 1024 /*align slack*/ + (size_t)S * 2 * kBBox + (size_t)kStages * kAStage +
+           (size_t)kEpiSlices * kCSm * kTM * 8;
   }
 };
 
@@ -225,8 +241,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* Bres = smem;                                   // [S][2] boxes of 8 KiB
-  uint8_t* Aring = smem + (size_t)S * 2 * kBBox;          // [kStages] boxes of 16 KiB
-  double* Cs = reinterpret_cast<double*>(Aring + (size_t)kStages * kABox);  // [2 halves][kCSm][kTM]
+  uint8_t* Aring = smem + (size_t)S * 2 * kBBox;          // [kStages] slices of 2 boxes of 16 KiB
+  double* Cs = reinterpret_cast<double*>(Aring + (size_t)kStages * kAStage);  // [kEpiSlices][kCSm][kTM]
   __shared__ __align__(8) uint64_t bar_bfull, bar_bempty, bar_full[kStages], bar_empty[kStages], bar_gready[8],
       bar_fin;
   __shared__ uint32_t s_tmem;
@@ -267,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the tile starts a new tile column (its U slices must be loaded)
   auto new_column = [&](int idx) { return idx == t_begin || (idx % tiles_m) == 0; };
 
-  int issued_uses[kStages] = {0, 0, 0, 0};
+  int issued_uses[kStages] = {};
   int b_issued = 0;
   if (warp == 0) {
     if (lane == 0) {
@@ -291,19 +307,19 @@ __global__ void __launch_bounds__(kThreads, 1)
               tc::tma_load_2d(Bres + (size_t)(t * 2 + kc) * kBBox, &mapB, kc * kKC, t * npad + c0, &bar_bfull);
         }
         bool ok = true;
-        for (int sl = 0; sl < S && ok; ++sl) {
-          for (int kc = 0; kc < nkc; ++kc, ++it) {
-            const int stage = it % kStages, use = it / kStages;
-            if (use > 0 && !tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
-              atomicExch(err, 11);
-              s_abort = 1;
-              ok = false;
-              break;
-            }
-            tc::mbar_arrive_expect_tx(&bar_full[stage], (uint32_t)kABox);
-            tc::tma_load_2d(Aring + (size_t)stage * kABox, &mapA, kc * kKC, sl * mpad + m0, &bar_full[stage]);
-            issued_uses[stage] = use + 1;
+        for (int sl = 0; sl < S; ++sl, ++it) {
+          const int stage = it % kStages, use = it / kStages;
+          if (use > 0 && !tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
+            atomicExch(err, 11);
+            s_abort = 1;
+            ok = false;
+            break;
           }
+          tc::mbar_arrive_expect_tx(&bar_full[stage], (uint32_t)(nkc * kABox));
+          for (int kc = 0; kc < nkc; ++kc)
+            tc::tma_load_2d(Aring + (size_t)stage * kAStage + (size_t)kc * kABox, &mapA, kc * kKC, sl * mpad + m0,
+                            &bar_full[stage]);
+          issued_uses[stage] = use + 1;
         }
         if (!ok) break;
       }
@@ -324,15 +340,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::tc_fence_after();
         }
-        for (int sl = 0; sl < S && ok; ++sl) {
-          for (int kc = 0; kc < nkc; ++kc, ++it) {
-            const int stage = it % kStages, use = it / kStages;
-            if (!tc::mbar_wait(&bar_full[stage], (uint32_t)(use & 1), kWaitNs)) {
-              ok = false;
-              break;
-            }
-            tc::tc_fence_after();
-            const uint64_t a0 = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kABox));
+        for (int sl = 0; sl < S && ok; ++sl, ++it) {
+          const int stage = it % kStages, use = it / kStages;
+          if (!tc::mbar_wait(&bar_full[stage], (uint32_t)(use & 1), kWaitNs)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          // one wait and two commits per slice: all k of the slice against every U slice t
+          for (int kc = 0; kc < nkc; ++kc) {
+            const uint64_t a0 = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kAStage + (size_t)kc * kABox));
             for (int t = 0; sl + t < S; ++t) {
               const uint32_t d = tmem + (uint32_t)(kTN * (sl + t));
               const uint64_t b0 = tc::desc_k128_sw128(tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox));
@@ -340,11 +357,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int k16 = 0; k16 < kKC / 16; ++k16)
                 tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
             }
-            if (!ok) break;
-            tc::mma_commit(&bar_empty[stage]);
           }
+          tc::mma_commit(&bar_empty[stage]);
           // digit group sl has received all of its terms
-          if (ok) tc::mma_commit(&bar_gready[sl]);
+          tc::mma_commit(&bar_gready[sl]);
         }
         if (!ok) {
           atomicExch(err, 21);
@@ -373,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue (warps 2..9)
     const int q = warp & 3;
-    const int h = (warp - 2) >> 2;   // column half of the tile
+    const int h = (warp - 2) >> 2;   // column slice of the tile
     const int r = q * 32 + lane;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16) + (uint32_t)(h * kEpiCols);
     double* Csh = Cs + (size_t)h * kCSm * kTM;
@@ -407,15 +423,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         tc::tc_fence_after();
         const int sh = 55 - 7 * (g + 2);
-        // two halves of 16 columns (keeps the live registers within one CTA per SM)
+        // 16 columns at a time (keeps the live registers within one CTA per SM)
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int half = 0; half < kEpiCols / 16; ++half) {
           uint32_t v[2][8];
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc)
             tc::tmem_ld8(lane_base + (uint32_t)(kTN * g + 16 * half + 8 * cc), v[cc]);
           tc::tmem_ld_wait();
-          if (g == S - 1 && half == 1) {
+          if (g == S - 1 && half == kEpiCols / 16 - 1) {
             // all of this tile's accumulators read by this warp: release them to the MMA warp
             tc::tc_fence_before();
             __syncwarp();
@@ -440,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // combine and store in batches of 8 columns; each batch's old C values are loaded
       // (from shared memory, or from global memory for the second half) before the
       // previous batch is computed, so the loads' latency overlaps the arithmetic
-      constexpr int kB = 8;
+      constexpr int kB = (kEpiSlices >= 4) ? 4 : 8;  // fewer live registers with more warps
       double cold[2][kB];
       auto load_batch = [&](int b, double (&dst)[kB]) {
 #pragma unroll
@@ -461,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int cl = b * kB + c, gj = c0 + cl;
           const int ec = __shfl_sync(0xffffffffu, ec_lane, cl);
           if (!row_ok || gj >= N || (gj >= skip_lo && gj < skip_hi) || T[cl] == 0) continue;
-          C[(int64_t)gi + (int64_t)gj * ldc] = cold[b & 1][c] + i64_times_pow2(T[cl], er + ec - 55);
+          C[(int64_t)gi + (int64_t)gj * ldc] = cold[b & 1][c] + i64_to_double_pow2(T[cl], er + ec - 55);
         }
       }
     }
