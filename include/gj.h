@@ -83,6 +83,10 @@ typedef struct gj_opts {
   double* pivots;        /* optional out [n], host or device: pivot value of step k (the
                             eq. 13 factors) */
   int64_t* fail_step;    /* optional out, host: failing step, -1 on success */
+  int32_t lookahead;     /* blocked path with tensor-core update: 0 = automatic (on for
+                            n >= 2048), 1 = off, 2 = on.  On: the next 128-column panel is
+                            reduced on a second stream while the rank-128 update of the
+                            other columns runs (same arithmetic, same results) */
 } gj_opts;
 
 /*

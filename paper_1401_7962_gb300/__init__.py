@@ -38,7 +38,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("tau", ctypes.c_double), ("panel", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("update", ctypes.c_int32), ("slices", ctypes.c_int32),
                 ("piv_rows", ctypes.c_void_p), ("piv_cols", ctypes.c_void_p), ("pivots", ctypes.c_void_p),
-                ("fail_step", ctypes.c_void_p)]
+                ("fail_step", ctypes.c_void_p), ("lookahead", ctypes.c_int32)]
 
 
 _LIB = None
@@ -158,7 +158,8 @@ def _stream_handle(stream) -> int:
 
 
 def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, path: int = PATH_AUTO,
-           panel: int = 0, update: int = UPDATE_AUTO, slices: int = 0, stream=None, record: bool = False):
+           panel: int = 0, update: int = UPDATE_AUTO, slices: int = 0, stream=None, record: bool = False,
+           lookahead: int = 0):
     """Invert one square matrix with ``gj_invert_ex``.
 
     ``A`` and ``out`` may live on the host or on the device (the library stages host
@@ -182,6 +183,7 @@ def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, pa
     o.path = int(path)
     o.update = int(update)
     o.slices = int(slices)
+    o.lookahead = int(lookahead)
     rec = {}
     fs = ctypes.c_int64(-1)
     if record:
@@ -227,7 +229,8 @@ def _rhs_ld(B, n) -> tuple[int, int]:
 
 
 def solve(A, B, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, path: int = PATH_AUTO,
-          panel: int = 0, update: int = UPDATE_AUTO, slices: int = 0, stream=None, record: bool = False):
+          panel: int = 0, update: int = UPDATE_AUTO, slices: int = 0, stream=None, record: bool = False,
+          lookahead: int = 0):
     """Solve ``A X = B`` with ``gj_solve_ex`` (one Gauss-Jordan sweep of ``[A | B]``).
 
     ``A`` (n x n) and ``B`` (n x m) column-major float64, host or device; ``out`` (n x m,
@@ -255,6 +258,7 @@ def solve(A, B, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, 
     o.path = int(path)
     o.update = int(update)
     o.slices = int(slices)
+    o.lookahead = int(lookahead)
     rec = {}
     fs = ctypes.c_int64(-1)
     if record:

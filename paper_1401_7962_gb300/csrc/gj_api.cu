@@ -107,7 +107,8 @@ static gj_status run_single_device(const gj_opts& o, int64_t n, const double* dA
       return launch_cta_single((int)n, dA, lda, dX, pivot_mode, o.tau, out, s);
     case 2:
       if (pivot_mode == GJ_PIVOT_FULL) return GJ_ERR_UNSUPPORTED;
-      return run_blocked(n, dA, lda, dX, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s);
+      return run_blocked(n, dA, lda, dX, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s, nullptr,
+                         o.lookahead);
     case 3:
       return run_unblocked(n, dA, lda, dX, pivot_mode, o.tau, out, s);
     default:
@@ -153,6 +154,7 @@ gj_status gj_invert_ex(const gj_opts* opts, int64_t n, const double* A, int64_t 
   if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
   if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
   if (o.path < 0 || o.path > 3 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8) return GJ_ERR_ARG;
+  if (o.lookahead < 0 || o.lookahead > 2) return GJ_ERR_ARG;
   if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
   if (n == 0) {
     if (det_sign) *det_sign = 1;
@@ -242,7 +244,8 @@ gj_status gj_solve_ex(const gj_opts* opts, int64_t n, int64_t nrhs, const double
   if (n < 0 || nrhs < 0 || lda < ld_min || ldb < ld_min || ldx < ld_min) return GJ_ERR_ARG;
   if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
   if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
-  if (o.path < 0 || o.path > 3 || o.path == 1 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8)
+  if (o.path < 0 || o.path > 3 || o.path == 1 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8 ||
+      o.lookahead < 0 || o.lookahead > 2)
     return GJ_ERR_ARG;
   if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
   if (n == 0) {
@@ -321,7 +324,8 @@ gj_status gj_solve_ex(const gj_opts* opts, int64_t n, int64_t nrhs, const double
     rhs.X = dX;
     rhs.ldx = dldx;
     if (path == 2)
-      GJ_TRY(run_blocked(n, dA, dlda, nullptr, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s, &rhs));
+      GJ_TRY(run_blocked(n, dA, dlda, nullptr, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s, &rhs,
+                         o.lookahead));
     else
       GJ_TRY(run_unblocked(n, dA, dlda, nullptr, pivot_mode, o.tau, out, s, &rhs));
 

@@ -23,8 +23,11 @@ struct Rhs {
 // update: 0 = automatic (tensor-core update from kTensorUpdateMinN), 1 = FP64 FMA, 2 = tensor
 // cores with `slices` digit slices (0 = 8).
 constexpr int kTensorUpdateMinN = 512;
+// lookahead: 0 = automatic (on for the tensor-core update from kLookaheadMinN), 1 = off, 2 = on.
+constexpr int kLookaheadMinN = 2048;
 gj_status run_blocked(int64_t n, const double* A, int64_t lda, double* X, int pivot_mode, double tau, int panel,
-                      int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs = nullptr);
+                      int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs = nullptr,
+                      int lookahead = 0);
 
 // Unblocked Gauss-Jordan over the whole grid, one rank-1 step per launch (any pivoting).
 gj_status run_unblocked(int64_t n, const double* A, int64_t lda, double* X, int pivot_mode, double tau,

@@ -23,6 +23,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <functional>
 #include <math.h>
 
 #include "gj_ozaki.cuh"
@@ -815,6 +816,18 @@ gj_status ws_alloc(T** p, size_t count, cudaStream_t s, void** list, int& nlist)
   return GJ_OK;
 }
 
+// Second stream and the two events of the look-ahead schedule; destroyed at scope exit
+// (destruction waits for nothing: the runtime releases them once pending work completes).
+struct StreamEvents {
+  cudaStream_t sb = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  ~StreamEvents() {
+    if (ev_a) cudaEventDestroy(ev_a);
+    if (ev_b) cudaEventDestroy(ev_b);
+    if (sb) cudaStreamDestroy(sb);
+  }
+};
+
 struct WsList {
   void* p[24];
   int n = 0;
@@ -857,7 +870,7 @@ static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* 
 }
 
 gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int pivot_mode, double tau, int panel,
-                      int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs) {
+                      int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs, int lookahead) {
   if (n64 > 46340) return GJ_ERR_UNSUPPORTED;
   const int n = (int)n64;
   const int64_t m = rhs ? rhs->m : 0;
@@ -872,6 +885,9 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   const bool tc = (update == 2) || (update == 0 && n >= kTensorUpdateMinN);
   const int S = slices > 0 ? slices : 8;
   const int Bw = tc ? 128 : b;
+  // look-ahead: the next outer panel is reduced on a second stream while the update of the
+  // other columns runs (tensor-core path with at least two outer panels)
+  const bool la = tc && n > Bw && (lookahead == 2 || (lookahead == 0 && n >= kLookaheadMinN));
 
   WsList ws(s);
   double *W, *Lbuf, *U, *pivots = out.pivots;
@@ -883,14 +899,19 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   GJ_WS(U, (size_t)nw * b);
   GJ_WS(posrow, (size_t)n);
   GJ_WS(rowat, (size_t)n);
-  GJ_WS(prow_ids, (size_t)Bw);
+  GJ_WS(prow_ids, (size_t)Bw * 2);  // two buffers: outer panels alternate (look-ahead)
   double* Mbuf;
   GJ_WS(Mbuf, (size_t)kPanelMaxB * kPanelMaxB);
   GJ_WS(oz_err, 4);
+  void* oz_ws_b = nullptr;  // the second stream's updates (columns of one outer panel)
   if (tc) {
     uint8_t* p8;
     GJ_WS(p8, ozaki_workspace_bytes(n, nw, S));
     oz_ws = p8;
+    if (la) {
+      GJ_WS(p8, ozaki_workspace_bytes(n, Bw, S));
+      oz_ws_b = p8;
+    }
   }
   if (!pivots) GJ_WS(pivots, (size_t)n);
   if (!piv_rows) GJ_WS(piv_rows, (size_t)n);
@@ -946,19 +967,28 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
     return GJ_OK;
   };
 
-  for (int K0 = 0; K0 < n; K0 += Bw) {
-    const int BB = (n - K0 < Bw) ? n - K0 : Bw;
+  // One outer panel [K0, K0 + BB): cluster sub-panels of width b, each followed by the
+  // fix-up of the rows pivoted earlier and (tensor path) the update of the rest of the outer
+  // panel.  pid receives the panel's pivot rows.  `after_first` runs once the first
+  // sub-panel is enqueued.
+  auto reduce_panel = [&](int K0, int BB, int* pid, cudaStream_t st_, void* ozw,
+                          const std::function<gj_status()>& after_first) -> gj_status {
     for (int k0 = K0; k0 < K0 + BB; k0 += b) {
       const int bb = (K0 + BB - k0 < b) ? K0 + BB - k0 : b;
       {
-        ProfScope ps(s, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
-        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, Mbuf, prow_ids + (k0 - K0),
-                                   pivots, piv_rows, out.status, out.fail_step, pivot_mode, tau));
+        ProfScope ps(st_, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
+        cfg.stream = st_;
+        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, Mbuf, pid + (k0 - K0), pivots,
+                                   piv_rows, out.status, out.fail_step, pivot_mode, tau));
       }
       prof_count(1);
+      if (k0 == K0 && after_first) {
+        gj_status st = after_first();
+        if (st != GJ_OK) return st;
+      }
       if (k0 > 0) {
-        ProfScope ps(s, "fixup_used_rows", 2.0 * k0 * (double)bb * bb, 16.0 * k0 * (double)bb);
-        fixup_used_rows_kernel<<<(n + 31) / 32, 256, 0, s>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
+        ProfScope ps(st_, "fixup_used_rows", 2.0 * k0 * (double)bb * bb, 16.0 * k0 * (double)bb);
+        fixup_used_rows_kernel<<<(n + 31) / 32, 256, 0, st_>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
         GJ_CUDA(cudaGetLastError());
         prof_count(1);
       }
@@ -966,37 +996,100 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
         gj_status st;
         if (tc) {
           // columns [K0, K0 + BB) of W; U = the sub-panel's pivot rows, zero on the sub-panel
-          st = ozaki_update(n, BB, bb, Lbuf, n, nullptr, W + (size_t)K0 * n, n, prow_ids + (k0 - K0), k0 - K0,
-                            k0 - K0 + bb, W + (size_t)K0 * n, n, S, oz_ws, oz_err, out.status, s);
+          st = ozaki_update(n, BB, bb, Lbuf, n, nullptr, W + (size_t)K0 * n, n, pid + (k0 - K0), k0 - K0,
+                            k0 - K0 + bb, W + (size_t)K0 * n, n, S, ozw, oz_err, out.status, st_);
         } else {
-          st = fp64_update(k0, bb, K0, K0 + BB, prow_ids + (k0 - K0));
+          st = fp64_update(k0, bb, K0, K0 + BB, pid + (k0 - K0));
         }
         if (st != GJ_OK) return st;
       }
     }
+    return GJ_OK;
+  };
+
+  // The rank-BB update of outer panel [K0, K0 + BB) on the columns outside [K0, K0 + skip)
+  // (inversion; skip >= BB) or right of K0 + skip (solving).
+  auto outer_update = [&](int K0, int BB, int skip, const int* pid, cudaStream_t st_, int max_ctas) -> gj_status {
     if (!solving) {
-      if (BB == n) continue;  // one panel covers every column: nothing outside it
-      if (tc) {
-        gj_status st = ozaki_update(n, n, BB, W + (size_t)K0 * n, n, prow_ids, W, n, prow_ids, K0, K0 + BB, W, n, S,
-                                    oz_ws, oz_err, out.status, s);
-        if (st != GJ_OK) return st;
-      } else {
-        gj_status st = fp64_update(K0, BB, 0, n, prow_ids);
-        if (st != GJ_OK) return st;
-      }
-    } else {
-      // solving: only the columns right of the panel (and the right-hand sides) matter
-      const int c0 = K0 + BB;
-      if (c0 >= nw) continue;
-      if (tc) {
-        gj_status st = ozaki_update(n, nw - c0, BB, W + (size_t)K0 * n, n, prow_ids, W + (size_t)c0 * n, n, prow_ids,
-                                    0, 0, W + (size_t)c0 * n, n, S, oz_ws, oz_err, out.status, s);
-        if (st != GJ_OK) return st;
-      } else {
-        gj_status st = fp64_update(K0, BB, c0, nw, prow_ids);
-        if (st != GJ_OK) return st;
-      }
+      const int zhi = std::min(n, K0 + skip);
+      if (K0 == 0 && zhi >= n) return GJ_OK;  // nothing outside
+      if (tc)
+        return ozaki_update(n, n, BB, W + (size_t)K0 * n, n, pid, W, n, pid, K0, zhi, W, n, S, oz_ws, oz_err,
+                            out.status, st_, max_ctas);
+      return fp64_update(K0, BB, 0, n, pid);
     }
+    const int c0 = K0 + skip;
+    if (c0 >= nw) return GJ_OK;
+    if (tc)
+      return ozaki_update(n, nw - c0, BB, W + (size_t)K0 * n, n, pid, W + (size_t)c0 * n, n, pid, 0, 0,
+                          W + (size_t)c0 * n, n, S, oz_ws, oz_err, out.status, st_, max_ctas);
+    return fp64_update(K0, BB, c0, nw, pid);
+  };
+
+  if (!la) {
+    for (int K0 = 0; K0 < n; K0 += Bw) {
+      const int BB = (n - K0 < Bw) ? n - K0 : Bw;
+      gj_status st = reduce_panel(K0, BB, prow_ids, s, oz_ws, nullptr);
+      if (st == GJ_OK) st = outer_update(K0, BB, BB, prow_ids, s, 0);
+      if (st != GJ_OK) return st;
+    }
+  } else {
+    // Stream sb reduces the panels and updates the next panel's columns (the narrow update);
+    // stream s runs the update of all other columns on a capped persistent grid, so that the
+    // cluster and sb's other kernels find free SMs.
+    // Panel p + 1 is reduced while the wide update of panel p runs.  Events:
+    //   ev_b (sb -> s): panel p reduced and panel p + 1's columns updated;
+    //   ev_a (s -> sb): wide update of panel p done (panel p + 2's columns current).
+    StreamEvents se;
+    GJ_CUDA(cudaStreamCreateWithFlags(&se.sb, cudaStreamNonBlocking));
+    GJ_CUDA(cudaEventCreateWithFlags(&se.ev_a, cudaEventDisableTiming));
+    GJ_CUDA(cudaEventCreateWithFlags(&se.ev_b, cudaEventDisableTiming));
+    cudaStream_t sb = se.sb;
+    GJ_CUDA(cudaEventRecord(se.ev_a, s));  // set-up done
+    GJ_CUDA(cudaStreamWaitEvent(sb, se.ev_a, 0));
+    // SMs left to sb: the cluster's plus room for its fix-ups and narrow updates (four
+    // cluster sizes measured best at n = 8192: the panel stream is the longer one)
+    const int wide_ctas = std::max(1, sms - std::min(4 * cs, sms / 2));
+    struct Pending {
+      bool valid = false;
+      int K0 = 0, BB = 0, skip = 0;
+      const int* pid = nullptr;
+    } pend;
+    auto submit_wide = [&]() -> gj_status {
+      if (!pend.valid) return GJ_OK;
+      pend.valid = false;
+      GJ_CUDA(cudaStreamWaitEvent(s, se.ev_b, 0));
+      gj_status st = outer_update(pend.K0, pend.BB, pend.skip, pend.pid, s, wide_ctas);
+      if (st != GJ_OK) return st;
+      GJ_CUDA(cudaEventRecord(se.ev_a, s));
+      return GJ_OK;
+    };
+    int p = 0;
+    for (int K0 = 0; K0 < n; K0 += Bw, ++p) {
+      const int BB = (n - K0 < Bw) ? n - K0 : Bw;
+      int* pid = prow_ids + (size_t)(p & 1) * Bw;
+      // the previous panel's wide update is enqueued once this panel's first cluster is
+      gj_status st = reduce_panel(K0, BB, pid, sb, oz_ws_b, submit_wide);
+      if (st != GJ_OK) return st;
+      const int K1 = K0 + BB;
+      const int BBn = (K1 < n) ? std::min(Bw, n - K1) : 0;
+      if (BBn > 0) {
+        // narrow update: panel p + 1's columns, after the wide update of panel p - 1
+        if (p > 0) GJ_CUDA(cudaStreamWaitEvent(sb, se.ev_a, 0));
+        st = ozaki_update(n, BBn, BB, W + (size_t)K0 * n, n, pid, W + (size_t)K1 * n, n, pid, 0, 0,
+                          W + (size_t)K1 * n, n, S, oz_ws_b, oz_err, out.status, sb);
+        if (st != GJ_OK) return st;
+      }
+      GJ_CUDA(cudaEventRecord(se.ev_b, sb));
+      pend.valid = true;
+      pend.K0 = K0;
+      pend.BB = BB;
+      pend.skip = BB + BBn;
+      pend.pid = pid;
+    }
+    gj_status st = submit_wide();  // the last panel's update; s then follows all of sb's work
+    if (st != GJ_OK) return st;
+    GJ_CUDA(cudaStreamWaitEvent(s, se.ev_b, 0));
   }
   fold_error_kernel<<<1, 1, 0, s>>>(oz_err, out.status);
   GJ_CUDA(cudaGetLastError());

@@ -550,7 +550,8 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S) {
 
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
-                       int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s) {
+                       int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s,
+                       int max_ctas) {
   if (K < 1 || K > kKB || S < 1 || S > 8) return GJ_ERR_ARG;
   const int64_t mpad = (M + kTM - 1) / kTM * kTM, npad = (N + kTM - 1) / kTM * kTM;
   uint8_t* p = static_cast<uint8_t*>(ws);
@@ -592,7 +593,7 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   }
   const int ntiles = tiles_m * (tiles_n - (ts_hi - ts_lo));
   if (ntiles <= 0) return GJ_OK;
-  const int grid = std::min(ntiles, sms);
+  const int grid = std::min(ntiles, (max_ctas > 0 && max_ctas < sms) ? max_ctas : sms);
   {
     ProfScope ps(s, "update_ozaki_tc", 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
                  16.0 * (double)M * (double)N);

@@ -68,7 +68,7 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.gj_invert(-3, p, 1, p, 1, ctypes.byref(sgn), ctypes.byref(lg)) == gj.ERR_ARG
     assert sgn.value == 0 and math.isinf(lg.value) and lg.value < 0
     # options: negative tau, unknown path / update, bad panel width
-    for field, val in (("tau", -1.0), ("path", 9), ("update", 7), ("panel", 48)):
+    for field, val in (("tau", -1.0), ("path", 9), ("update", 7), ("panel", 48), ("lookahead", 3)):
         o = gj._Opts()
         setattr(o, field, val)
         assert L.gj_invert_ex(ctypes.byref(o), 2, p, 2, p + 64, 1, None, None) == gj.ERR_ARG

@@ -85,6 +85,30 @@ def test_blocked_random(n, panel, mode, update):
     assert_matches_oracle(A, r, o, mode)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n,panel", [(300, 32), (1031, 16), (2100, 0)])
+def test_lookahead_matches_oracle_and_sequential_schedule(n, panel, mode):
+    """The look-ahead schedule (next outer panel reduced on a second stream during the wide
+    update) runs the same kernels on the same operands: results bitwise equal to the
+    sequential schedule, and parity with the oracle."""
+    seed, A, o = tie_free_seed(make_input(n, mode, 0), 2700 + n, mode)
+    on = run(A, mode, path=gj.PATH_BLOCKED, panel=panel, update=gj.UPDATE_TC_OZAKI, lookahead=2)
+    off = run(A, mode, path=gj.PATH_BLOCKED, panel=panel, update=gj.UPDATE_TC_OZAKI, lookahead=1)
+    assert np.array_equal(on["X"], off["X"])
+    assert on["det_log2"] == off["det_log2"] and on["det_sign"] == off["det_sign"]
+    assert np.array_equal(on["piv_rows"], off["piv_rows"])
+    assert_matches_oracle(A, on, o, mode)
+
+
+def test_lookahead_failure_is_reported():
+    """A singular input stops both streams: the status, failing step and det come back."""
+    n = 700
+    A = wl.gaussian(n, 2800)
+    A[:, 400] = 0.0
+    r = run(A, 1, path=gj.PATH_BLOCKED, update=gj.UPDATE_TC_OZAKI, lookahead=2)
+    assert r["status"] == gj.SINGULAR and r["fail_step"] == 400 and r["det_sign"] == 0
+
+
 @pytest.mark.parametrize("slices", [7, 8])
 def test_blocked_tensor_update_slices(slices):
     """7 digit slices (49 bits) still meet the parity bar on a well-conditioned input; 6 (42

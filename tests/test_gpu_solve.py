@@ -95,6 +95,16 @@ def test_blocked_solve_update_engines(n, update):
     check(A, B, r, o, 1)
 
 
+@pytest.mark.parametrize("lookahead", [1, 2])
+def test_solve_lookahead(lookahead):
+    n, m = 1100, 7
+    seed, A, _ = tie_free_seed(lambda s: wl.gaussian(n, s), 9500, 1)
+    B = rhs(n, m, seed)
+    o = oracle.solve(A, B, 1)
+    r = gj.solve(dev(A), dev(B), 1, update=gj.UPDATE_TC_OZAKI, lookahead=lookahead, record=True)
+    check(A, B, r, o, 1)
+
+
 @pytest.mark.parametrize("n", [1, 5, 64, 130, 257])
 @pytest.mark.parametrize("m", [1, 9])
 def test_full_pivoting_solve_matches_oracle(n, m):
