@@ -46,7 +46,9 @@ FP64_NOMINAL_GFLOPS = 1250.0
 # when its kernel changes, until it is captured again.
 NCU_TRAFFIC = {
     "update_dfma": None,  # column-window change since profiles/update_dfma_inv6144.md
-    "update_ozaki_tc": None,  # kernel changed since the last capture
+    # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (88 CTAs)
+    "update_ozaki_wide": {"n": 6144, "bytes": 323.219968e6 + 233.586944e6},
+    "update_ozaki_tc": None,
     # the plan replays one kernel per order bin; traffic summed over those kernels
     "batched_plan": None,
 }
@@ -293,7 +295,8 @@ def run_gpu(args) -> None:
         st = torch.zeros(count, dtype=torch.int32, device=dev)
         sg = torch.zeros(count, dtype=torch.int8, device=dev)
         lg = torch.zeros(count, dtype=torch.float64, device=dev)
-        plan = gj.BatchedPlan(sizes, W["pivot"])  # autotuned kernel variant per order bin
+        # autotuned kernel variant per order bin (choices read from / written to --tune-cache)
+        plan = gj.BatchedPlan(sizes, W["pivot"], tune_cache=args.tune_cache)
         extra["bins"] = [{k: b[k] for k in ("lo", "hi", "count", "variant")} for b in plan.bins()]
         flops_step = float((2.0 * sizes.astype(np.float64) ** 3).sum())
         bytes_step = float(16.0 * (sizes.astype(np.float64) ** 2).sum())
@@ -389,9 +392,11 @@ def run_gpu(args) -> None:
         unit = "GFLOP/s"
 
     roof = None
-    if "update_ozaki_tc" in prof and prof["update_ozaki_tc"]["launches"]:
-        dominant = "update_ozaki_tc"
-    if dominant == "update_ozaki_tc":
+    for name in ("update_ozaki_wide", "update_ozaki_tc"):
+        if name in prof and prof[name]["launches"]:
+            dominant = name
+            break
+    if dominant in ("update_ozaki_wide", "update_ozaki_tc"):
         d = prof[dominant]
         avg_ms = d["total_ms"] / d["launches"]
         S = args.slices or 8
@@ -406,6 +411,12 @@ def run_gpu(args) -> None:
         roof["kernel"] = dominant
         roof["avg_launch_ms"] = round(avg_ms, 6)
         roof["share_of_step"] = round(d["total_ms"] / ms, 4)
+        if dominant == "update_ozaki_wide" and W["n"] >= 2048:
+            cs = min(16, -(-W["n"] // 256))
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            roof["grid_sms"] = sms - min(4 * cs, sms // 2)
+            roof["note"] = (f"look-ahead: runs on {roof['grid_sms']} of {sms} SMs while the panel stream reduces "
+                            "the next panel; share_of_step counts overlapped time")
     elif dominant in prof and prof[dominant]["launches"]:
         d = prof[dominant]
         avg_ms = d["total_ms"] / d["launches"]
@@ -613,6 +624,8 @@ def main():
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--tune-cache", default=None,
+                    help="text file for the batched plan's autotuner choices (reused when present)")
     ap.add_argument("--count", type=int, default=0,
                     help="matrices in the batched workload (default: the workload's own); for profiling runs")
     ap.add_argument("--n", type=int, default=0,

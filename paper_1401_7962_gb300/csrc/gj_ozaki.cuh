@@ -15,10 +15,11 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S);
 // columns of C are left untouched.  `ws` holds ozaki_workspace_bytes(M, N, S); `err`
 // receives a nonzero code if a bounded device wait expired; kernels return at once when
 // *status != GJ_OK (status may be null).  max_ctas > 0 caps the persistent grid (one CTA
-// per SM), leaving the other SMs to work on another stream.
+// per SM), leaving the other SMs to work on another stream.  prof_name labels the launch for
+// the library's profiling hooks.
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
                        int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s,
-                       int max_ctas = 0);
+                       int max_ctas = 0, const char* prof_name = "update_ozaki_tc");
 
 }  // namespace gj

@@ -997,7 +997,8 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
         if (tc) {
           // columns [K0, K0 + BB) of W; U = the sub-panel's pivot rows, zero on the sub-panel
           st = ozaki_update(n, BB, bb, Lbuf, n, nullptr, W + (size_t)K0 * n, n, pid + (k0 - K0), k0 - K0,
-                            k0 - K0 + bb, W + (size_t)K0 * n, n, S, ozw, oz_err, out.status, st_);
+                            k0 - K0 + bb, W + (size_t)K0 * n, n, S, ozw, oz_err, out.status, st_, 0,
+                            "update_ozaki_panel");
         } else {
           st = fp64_update(k0, bb, K0, K0 + BB, pid + (k0 - K0));
         }
@@ -1015,14 +1016,14 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
       if (K0 == 0 && zhi >= n) return GJ_OK;  // nothing outside
       if (tc)
         return ozaki_update(n, n, BB, W + (size_t)K0 * n, n, pid, W, n, pid, K0, zhi, W, n, S, oz_ws, oz_err,
-                            out.status, st_, max_ctas);
+                            out.status, st_, max_ctas, "update_ozaki_wide");
       return fp64_update(K0, BB, 0, n, pid);
     }
     const int c0 = K0 + skip;
     if (c0 >= nw) return GJ_OK;
     if (tc)
       return ozaki_update(n, nw - c0, BB, W + (size_t)K0 * n, n, pid, W + (size_t)c0 * n, n, pid, 0, 0,
-                          W + (size_t)c0 * n, n, S, oz_ws, oz_err, out.status, st_, max_ctas);
+                          W + (size_t)c0 * n, n, S, oz_ws, oz_err, out.status, st_, max_ctas, "update_ozaki_wide");
     return fp64_update(K0, BB, c0, nw, pid);
   };
 
@@ -1077,7 +1078,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
         // narrow update: panel p + 1's columns, after the wide update of panel p - 1
         if (p > 0) GJ_CUDA(cudaStreamWaitEvent(sb, se.ev_a, 0));
         st = ozaki_update(n, BBn, BB, W + (size_t)K0 * n, n, pid, W + (size_t)K1 * n, n, pid, 0, 0,
-                          W + (size_t)K1 * n, n, S, oz_ws_b, oz_err, out.status, sb);
+                          W + (size_t)K1 * n, n, S, oz_ws_b, oz_err, out.status, sb, 0, "update_ozaki_panel");
         if (st != GJ_OK) return st;
       }
       GJ_CUDA(cudaEventRecord(se.ev_b, sb));

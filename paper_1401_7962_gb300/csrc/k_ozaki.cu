@@ -551,7 +551,7 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S) {
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
                        int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s,
-                       int max_ctas) {
+                       int max_ctas, const char* prof_name) {
   if (K < 1 || K > kKB || S < 1 || S > 8) return GJ_ERR_ARG;
   const int64_t mpad = (M + kTM - 1) / kTM * kTM, npad = (N + kTM - 1) / kTM * kTM;
   uint8_t* p = static_cast<uint8_t*>(ws);
@@ -595,7 +595,7 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   if (ntiles <= 0) return GJ_OK;
   const int grid = std::min(ntiles, (max_ctas > 0 && max_ctas < sms) ? max_ctas : sms);
   {
-    ProfScope ps(s, "update_ozaki_tc", 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
+    ProfScope ps(s, prof_name, 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
                  16.0 * (double)M * (double)N);
     ozaki_update_kernel<<<grid, kThreads, smem, s>>>(mapA, mapB, (int)M, (int)N, (int)mpad, (int)npad, S, nkc,
                                                     tiles_m, tiles_n, ts_lo, ts_hi, zero_lo, zero_hi, C, ldc, erow,
