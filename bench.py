@@ -56,7 +56,7 @@ NCU_TRAFFIC = {
 WORKLOADS = {
     "inv8192": dict(n=8192, shift=0.1, pivot=1, seed=wl.SEED_BASE + 2,
                     name="gj-inverse-8192-fp64-partial-blocked"),
-    "inv128": dict(n=128, shift=0.0, pivot=2, seed=wl.SEED_BASE + 1, name="gj-inverse-128-fp64-full-cta"),
+    "inv128": dict(n=128, shift=0.0, pivot=2, seed=wl.SEED_BASE + 1, name="gj-inverse-128-fp64-full-cluster"),
     "batch200k": dict(count=200_000, seed=wl.SEED_BASE + 3, pivot=1,
                       name="gj-batched-200k-n4to64-fp64-partial"),
     "mixed16384": dict(n=16384, kappa=1e6, pivot=1, seed=wl.SEED_BASE + 4,
@@ -346,7 +346,7 @@ def run_gpu(args) -> None:
                 raise RuntimeError(f"gj_invert_ex failed: {gj.status_string(stc)} {gj.last_error()}")
 
         opts.slices = args.slices
-        dominant = "update_dfma" if args.workload == "inv8192" else "cta_single"
+        dominant = "update_dfma" if args.workload == "inv8192" else "cluster_single"
         h2d = d2h = n * n * 8
 
     # ---- warm-up
@@ -472,7 +472,7 @@ def run_gpu(args) -> None:
     if rank == 0:
         cfg = {"workload": W["name"], "pivot": ["none", "partial", "full"][W["pivot"]],
                "l2": "inputs larger than L2 (no flush)" if args.workload != "inv128" else
-               "128 KiB matrix is L2-resident; latency-bound single CTA (no flush)",
+               "128 KiB matrix is L2-resident; latency-bound 16-CTA cluster (no flush)",
                "profile": prof}
         if args.workload == "inv8192":
             eng = "fp64 fma" if (args.update == "dfma") else \
@@ -485,7 +485,8 @@ def run_gpu(args) -> None:
                         "method": "reduced-precision blocked GJ (tensor update, x0 slices) + Newton-Schulz, "
                                   "FP64-level residual"})
         elif args.workload == "inv128":
-            cfg.update({"n": W["n"], "input": "N(0,1), seed 1402"})
+            cfg.update({"n": W["n"], "input": "N(0,1), seed 1402",
+                        "kernel": "one 16-CTA cluster, rows spread over its CTAs (FP64 of 16 SMs)"})
         else:
             cfg.update({"count": W["count"], "orders": "U{4..64}", "input": "U[-1,1], diag 1+sum|row|, seed 1404",
                         "launch": "plan + CUDA graph"})

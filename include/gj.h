@@ -70,7 +70,8 @@ typedef struct gj_opts {
                             choice.  Ignored by the single-CTA path */
   int32_t path;          /* 0 = automatic; 1 = single-CTA shared-memory kernel (n <= 128);
                             2 = blocked panel + rank-b update (partial / none pivoting);
-                            3 = unblocked multi-CTA (any pivoting, any n) */
+                            3 = unblocked multi-CTA (any pivoting, any n); 4 = one
+                            thread-block cluster, rows spread over its CTAs (n <= 128) */
   int32_t update;        /* blocked path rank-b update engine: 0 = automatic (tensor cores for
                             n >= 512), 1 = FP64 FMA, 2 = FP64 emulated on BF16 tcgen05 tensor
                             cores (digit-split operands, exact FP32 partial sums, FP64
@@ -311,6 +312,14 @@ typedef struct gj_profile_entry {
 
 gj_status gj_profile_begin(void);
 int gj_profile_end(gj_profile_entry* out, int max_entries, int64_t* launches);
+
+/*
+ * gj_trim_memory -- return the device memory the library keeps between calls.  Workspace
+ * is taken, stream-ordered, from a memory pool of the library's own on each device that
+ * keeps freed memory for later calls (up to the largest amount one call has needed).  The
+ * paper has no counterpart.  Call it with no library work in flight.
+ */
+gj_status gj_trim_memory(void);
 
 /* gj_status_string -- static text for a status code. */
 const char* gj_status_string(int status);

@@ -22,7 +22,7 @@ __all__ = ["lib", "invert", "invert_mixed", "invert_batched", "invert_batched_no
 OK, SINGULAR, ZERO_PIVOT, NONFINITE, NOT_CONVERGED = 0, 1, 2, 3, 4
 ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 PIVOT_NONE, PIVOT_PARTIAL, PIVOT_FULL = 0, 1, 2
-PATH_AUTO, PATH_CTA, PATH_BLOCKED, PATH_UNBLOCKED = 0, 1, 2, 3
+PATH_AUTO, PATH_CTA, PATH_BLOCKED, PATH_UNBLOCKED, PATH_CLUSTER = 0, 1, 2, 3, 4
 BATCHED_WARP4, BATCHED_WARP8, BATCHED_CTA64, BATCHED_CTA128, BATCHED_CTA256, BATCHED_CTA512 = range(6)
 BATCHED_NAMES = ["warp4", "warp8", "cta64", "cta128", "cta256", "cta512"]
 UPDATE_AUTO, UPDATE_DFMA, UPDATE_TC_OZAKI = 0, 1, 2
@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
     L.gj_last_error.argtypes = []
     L.gj_version.restype = ctypes.c_char_p
     L.gj_version.argtypes = []
+    L.gj_trim_memory.restype = I
+    L.gj_trim_memory.argtypes = []
     _LIB = L
     return L
 

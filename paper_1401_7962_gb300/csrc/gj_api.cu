@@ -20,6 +20,39 @@ static thread_local char g_last_error[512] = "";
 
 void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pools[dev], &props);
+      if (e != cudaSuccess) {
+        g_pools[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = ~0ull;  // keep freed memory for the next call
+      cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = g_pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 gj_status cuda_fail(cudaError_t e, const char* what) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
   return GJ_ERR_CUDA;
@@ -50,7 +83,7 @@ class Scratch {
   gj_status alloc(T** out, size_t count) {
     void* p = nullptr;
     size_t bytes = sizeof(T) * (count > 0 ? count : 1);
-    cudaError_t e = cudaMallocAsync(&p, bytes, s_);
+    cudaError_t e = lib_malloc_async(&p, bytes, s_);
     if (e != cudaSuccess) {
       cudaGetLastError();
       snprintf(g_last_error, sizeof(g_last_error), "cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
@@ -89,7 +122,7 @@ static gj_status run_single_device(const gj_opts& o, int64_t n, const double* dA
                                    ResultBlock* res, cudaStream_t s) {
   int path = o.path;
   if (path == 0) {
-    if (n <= kCtaMaxN) path = 1;
+    if (n <= kCtaMaxN) path = (n >= 64) ? 4 : 1;  // a cluster beats one SM's FP64 units from n = 64
     else if (pivot_mode == GJ_PIVOT_FULL) path = 3;
     else path = 2;
   }
@@ -111,6 +144,9 @@ static gj_status run_single_device(const gj_opts& o, int64_t n, const double* dA
                          o.lookahead);
     case 3:
       return run_unblocked(n, dA, lda, dX, pivot_mode, o.tau, out, s);
+    case 4:
+      if (n > kCtaMaxN) return GJ_ERR_UNSUPPORTED;
+      return launch_cluster_single((int)n, dA, lda, dX, pivot_mode, o.tau, out, s);
     default:
       return GJ_ERR_ARG;
   }
@@ -123,6 +159,16 @@ using namespace gj;
 extern "C" {
 
 const char* gj_version(void) { return "gj-gb300 0.1 (sm_103a)"; }
+
+gj_status gj_trim_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (int d = 0; d < kMaxDevices; ++d)
+    if (g_pools[d]) {
+      cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolTrimTo");
+    }
+  return GJ_OK;
+}
 
 const char* gj_last_error(void) { return g_last_error; }
 
@@ -153,7 +199,7 @@ gj_status gj_invert_ex(const gj_opts* opts, int64_t n, const double* A, int64_t 
   if (n < 0 || lda < (n > 0 ? n : 1)) return GJ_ERR_ARG;
   if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
   if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
-  if (o.path < 0 || o.path > 3 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8) return GJ_ERR_ARG;
+  if (o.path < 0 || o.path > 4 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8) return GJ_ERR_ARG;
   if (o.lookahead < 0 || o.lookahead > 2) return GJ_ERR_ARG;
   if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
   if (n == 0) {

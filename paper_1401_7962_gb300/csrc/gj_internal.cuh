@@ -88,12 +88,21 @@ struct CtaOut {
 };
 
 // Largest order handled by one CTA in shared memory.
+// Stream-ordered allocation from the library's own memory pool on the current device.  The
+// pool keeps freed memory for the next call (the default pool returns it to the driver at
+// every synchronisation, which made each call pay for fresh allocations); gj_trim_memory
+// releases it.
+cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t s);
+
 constexpr int kCtaMaxN = 128;
 
 // Shared memory needed by the single-CTA kernel for orders up to nmax.
 size_t cta_smem_bytes(int nmax);
 
 // One matrix, one CTA.  A (ld lda) -> X (ld n); X may equal A when lda == n.
+// One matrix (n <= 128) on a thread-block cluster (k_cluster.cu), rows spread over its CTAs.
+gj_status launch_cluster_single(int n, const double* A, int64_t lda, double* X, int pivot_mode, double tau,
+                                const CtaOut& out, cudaStream_t s);
 gj_status launch_cta_single(int n, const double* A, int64_t lda, double* X, int pivot_mode, double tau,
                             const CtaOut& out, cudaStream_t s);
 

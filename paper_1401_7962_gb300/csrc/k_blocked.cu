@@ -28,6 +28,7 @@
 
 #include "gj_ozaki.cuh"
 #include "gj_paths.cuh"
+#include "cluster_ptx.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -50,7 +51,6 @@ struct __align__(16) PanelCand {
 
 constexpr int kSlots = 3;        // candidate slots: pushes for step t+1 and reads of step t never collide
 constexpr int kRowBlock = 32;    // rows are dealt to the cluster CTAs in blocks of 32, round robin
-constexpr uint64_t kPanelWaitNs = 2000000000ull;
 
 struct PanelSmem {
   static size_t bytes(int cs, int rp, int bb) {
@@ -65,48 +65,6 @@ struct PanelSmem {
 // Global row of local row il of cluster CTA `rank` (block-cyclic distribution).
 __device__ __forceinline__ int panel_row(int il, int rank, int cs) {
   return ((il / kRowBlock) * cs + rank) * kRowBlock + (il % kRowBlock);
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint32_t map_rank(uint32_t local, int rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-  return r;
-}
-// 16-byte store into another CTA's shared memory, counted in bytes on that CTA's mbarrier.
-__device__ __forceinline__ void st_async16(uint32_t raddr, int4 v, uint32_t rbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
-               ::"r"(raddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar)
-               : "memory");
-}
-__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t c) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(c) : "memory");
-}
-__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
-  auto once = [&]() {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-  };
-  if (once()) return true;
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (;;) {
-    if (once()) return true;
-    uint64_t t1;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-    if (t1 - t0 > kPanelWaitNs) return false;
-  }
 }
 
 __device__ __forceinline__ void consider3(double v, int key, int il, uint64_t& bv, int& bk, int& bi) {
@@ -806,7 +764,7 @@ int num_sms() {
 template <class T>
 gj_status ws_alloc(T** p, size_t count, cudaStream_t s, void** list, int& nlist) {
   void* q = nullptr;
-  cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (count > 0 ? count : 1), s);
+  cudaError_t e = lib_malloc_async(&q, sizeof(T) * (count > 0 ? count : 1), s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return GJ_ERR_NOMEM;

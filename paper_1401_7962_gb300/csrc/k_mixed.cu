@@ -142,7 +142,7 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
     cudaStreamSynchronize(s);
   };
   auto alloc = [&](void** p, size_t bytes) {
-    if (cudaMallocAsync(p, bytes, s) != cudaSuccess) {
+    if (lib_malloc_async(p, bytes, s) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }

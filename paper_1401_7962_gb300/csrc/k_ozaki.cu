@@ -621,7 +621,7 @@ extern "C" gj_status gj_gemm_update_emulated(int64_t M, int64_t N, int64_t K, co
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* ws = nullptr;
   const size_t bytes = ozaki_workspace_bytes(M, N, slices) + 16;
-  cudaError_t e = cudaMallocAsync(&ws, bytes, s);
+  cudaError_t e = lib_malloc_async(&ws, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return GJ_ERR_NOMEM;

@@ -44,7 +44,7 @@ def make_input(n, mode, seed):
     return lambda s: wl.gaussian(n, s, shift=shift)
 
 
-@pytest.mark.parametrize("path", [gj.PATH_CTA, gj.PATH_UNBLOCKED])
+@pytest.mark.parametrize("path", [gj.PATH_CTA, gj.PATH_UNBLOCKED, gj.PATH_CLUSTER])
 def test_paper_example(path):
     g = json.load(open(os.path.join(GOLDEN, "paper_example_3x3.json")))
     A = np.array(g["A"], dtype=np.float64)
@@ -83,6 +83,34 @@ def test_blocked_random(n, panel, mode, update):
     seed, A, o = tie_free_seed(make_input(n, mode, 0), 2000 + n, mode)
     r = run(A, mode, path=gj.PATH_BLOCKED, panel=panel, update=update)
     assert_matches_oracle(A, r, o, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 31, 47, 48, 64, 95, 96, 127, 128])
+def test_cluster_path_matches_oracle_and_cta_kernel(n, mode):
+    """The cluster kernel (rows spread over 4-16 CTAs) runs the single-CTA kernel's arithmetic:
+    bitwise equal results, pivots identical to the oracle on tie-free inputs."""
+    seed, A, o = tie_free_seed(make_input(n, mode, 0), 3000 + n, mode)
+    r = run(A, mode, path=gj.PATH_CLUSTER)
+    c = run(A, mode, path=gj.PATH_CTA)
+    assert np.array_equal(r["X"], c["X"])
+    assert r["det_log2"] == c["det_log2"] and r["det_sign"] == c["det_sign"]
+    assert np.array_equal(r["piv_rows"], c["piv_rows"]) and np.array_equal(r["piv_cols"], c["piv_cols"])
+    assert_matches_oracle(A, r, o, mode)
+
+
+def test_cluster_path_failures():
+    S = np.array([[0.0, 1.0], [1.0, 0.0]])
+    assert run(S, 0, path=gj.PATH_CLUSTER)["status"] == gj.ZERO_PIVOT
+    Z = wl.gaussian(100, 3100)
+    Z[:, 60] = 0.0
+    for mode in (1, 2):
+        r = run(Z, mode, path=gj.PATH_CLUSTER)
+        c = run(Z, mode, path=gj.PATH_CTA)
+        assert r["status"] == gj.SINGULAR and r["status"] == c["status"] and r["fail_step"] == c["fail_step"]
+    N = np.eye(64)
+    N[5, 3] = np.inf
+    assert run(N, 2, path=gj.PATH_CLUSTER)["status"] == gj.NONFINITE
 
 
 @pytest.mark.parametrize("mode", [0, 1])
