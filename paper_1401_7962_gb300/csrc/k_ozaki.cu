@@ -309,7 +309,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int sl = 0; sl < S; ++sl, ++it) {
           const int stage = it % kStages, use = it / kStages;
-          if (use > 0 && !tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs)) {
+          // the stage's previous slice must be consumed: with S >= kStages that slice's
+          // group barrier says so (slice sl - 2 of this tile, or slice S - 2 + sl of the
+          // previous one); with fewer slices a per-stage barrier is committed instead
+          bool free_ok = true;
+          if (use > 0) {
+            if (S >= kStages) {
+              const int g = (sl >= kStages) ? sl - kStages : S - kStages + sl;
+              const int tl = (sl >= kStages) ? local : local - 1;
+              free_ok = tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(tl & 1), kWaitNs);
+            } else {
+              free_ok = tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs);
+            }
+          }
+          if (!free_ok) {
             atomicExch(err, 11);
             s_abort = 1;
             ok = false;
@@ -358,8 +371,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
             }
           }
-          tc::mma_commit(&bar_empty[stage]);
-          // digit group sl has received all of its terms
+          if (S < kStages) tc::mma_commit(&bar_empty[stage]);
+          // digit group sl has received all of its terms (and, with S >= kStages, the
+          // stage of slice sl is free again)
           tc::mma_commit(&bar_gready[sl]);
         }
         if (!ok) {
@@ -415,10 +429,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int c = 0; c < kEpiCols; ++c) T[c] = 0;
       bool ok = true;
-      for (int g = 0; g < S; ++g) {
-        // one lane polls, the warp follows
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {  // unrolled: each group's shift is a constant
+        if (g >= S) break;
+        // one lane polls, the warp follows; the last group gates the next tile's MMAs, so it
+        // is polled without sleeping
         int ok0 = 0;
-        if (lane == 0) ok0 = tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(local & 1), kWaitNs) && !s_abort;
+        if (lane == 0)
+          ok0 = ((g == S - 1) ? tc::mbar_wait(&bar_gready[g], (uint32_t)(local & 1), kWaitNs)
+                              : tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(local & 1), kWaitNs)) &&
+                !s_abort;
         ok = __shfl_sync(0xffffffffu, ok0, 0) != 0;  // warp-uniform
         if (!ok) break;
         tc::tc_fence_after();
