@@ -414,7 +414,7 @@ def run_gpu(args) -> None:
         if dominant == "update_ozaki_wide" and W["n"] >= 2048:
             cs = min(16, -(-W["n"] // 256))
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            roof["grid_sms"] = sms - min(4 * cs, sms // 2)
+            roof["grid_sms"] = sms - min((7 * cs) // 2, sms // 2)
             roof["note"] = (f"look-ahead: runs on {roof['grid_sms']} of {sms} SMs while the panel stream reduces "
                             "the next panel; share_of_step counts overlapped time")
     elif dominant in prof and prof[dominant]["launches"]:

@@ -340,49 +340,60 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   cluster.sync();  // no CTA leaves while stores into its shared memory may be in flight
 }
 
-// Rows pivoted before the panel (position < k0): W[i, P] <- -W[i, P] M^-1 with
-// M^-1[s, t] = Mbuf[s * 64 + t] (the panel's pivot block, written by the panel); L gets the
-// same values (these rows are not pivot rows of the panel).  A warp takes 32 consecutive
-// rows and one column t, so loads and stores are coalesced and M^-1[., t] is a broadcast.
+// Rows pivoted before the panel (position < k0): L[i, :] <- -W[i, P] M^-1 with
+// M^-1[s, t] = Mbuf[s * 64 + t] (the panel's pivot block, written by the panel); these rows
+// are not pivot rows of the panel.  Block (x, y) takes 64 consecutive rows and the 8 columns
+// 8y .. 8y + 7 of the result, so that the FP64 work spreads over as many SMs as the rows
+// allow; the rows' panel values are staged in shared memory with coalesced loads, thread
+// (r, q) forms row r, columns 8y + 2q and 8y + 2q + 1.  Blocks of the same rows read W[i, P]
+// while others write their results, so the results go to L only; fixup_store_kernel then
+// copies them into W[i, P].
+constexpr int kFixRows = 64, kFixCols = 8;
 __global__ void __launch_bounds__(256) fixup_used_rows_kernel(int n, int k0, int bb, double* __restrict__ W,
                                                               const int* __restrict__ posrow,
                                                               const double* __restrict__ Mbuf,
                                                               double* __restrict__ Lbuf, const int32_t* status) {
   if (*status != GJ_OK || k0 == 0) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + lane;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int r0 = blockIdx.x * kFixRows, t0 = blockIdx.y * kFixCols;
+  const int r = tid % kFixRows, q = tid / kFixRows;  // row in the block, column pair
+  const int i = r0 + r;
   const bool used = i < n && posrow[i] < k0;
-  if (!__syncthreads_or(used)) return;  // uniform over the block (same 32 rows in every warp)
-  __shared__ double Minv[kPanelMaxB][kPanelMaxB];
-  for (int e = threadIdx.x; e < bb * kPanelMaxB; e += blockDim.x) Minv[e / kPanelMaxB][e % kPanelMaxB] = Mbuf[e];
-  __syncthreads();
-  double o[kPanelMaxB];
+  if (!__syncthreads_or(used)) return;  // no row of this block was pivoted earlier
+  __shared__ double Minv[kPanelMaxB][kFixCols];
+  __shared__ double Nt[kPanelMaxB][kFixRows + 1];  // Nt[s][r] = W[r0 + r, k0 + s]
+  for (int e = tid; e < bb * kFixCols; e += blockDim.x) {
+    const int s2 = e / kFixCols, c = e % kFixCols;
+    Minv[s2][c] = (t0 + c < bb) ? Mbuf[s2 * kPanelMaxB + t0 + c] : 0.0;
+  }
+  for (int s2 = w; s2 < bb; s2 += 8) {
 #pragma unroll
-  for (int s2 = 0; s2 < kPanelMaxB; ++s2)
-    o[s2] = (used && s2 < bb) ? W[(int64_t)i + (int64_t)(k0 + s2) * n] : 0.0;
-  double acc[kPanelMaxB / 8];
-#pragma unroll
-  for (int c = 0; c < kPanelMaxB / 8; ++c) acc[c] = 0.0;
-  // warp w of 8 handles columns t = w, w + 8, ...
-#pragma unroll
-  for (int s2 = 0; s2 < kPanelMaxB; ++s2) {
-    if (s2 >= bb) break;
-#pragma unroll
-    for (int c = 0; c < kPanelMaxB / 8; ++c) {
-      const int t2 = w + 8 * c;
-      if (t2 < bb) acc[c] = fma(o[s2], Minv[s2][t2], acc[c]);
+    for (int h = 0; h < 2; ++h) {
+      const int rr = lane + 32 * h, ii = r0 + rr;
+      Nt[s2][rr] = (ii < n) ? W[(int64_t)ii + (int64_t)(k0 + s2) * n] : 0.0;
     }
   }
-  __syncwarp();
-  __syncthreads();  // every old value read before any column is overwritten
+  __syncthreads();
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int s2 = 0; s2 < bb; ++s2) {
+    const double a = Nt[s2][r];
+    acc0 = fma(a, Minv[s2][2 * q], acc0);
+    acc1 = fma(a, Minv[s2][2 * q + 1], acc1);
+  }
   if (!used) return;
-#pragma unroll
-  for (int c = 0; c < kPanelMaxB / 8; ++c) {
-    const int t2 = w + 8 * c;
-    if (t2 < bb) {
-      W[(int64_t)i + (int64_t)(k0 + t2) * n] = -acc[c];
-      Lbuf[(int64_t)i + (int64_t)t2 * n] = -acc[c];
-    }
+  const int ta = t0 + 2 * q;
+  if (ta < bb) Lbuf[(int64_t)i + (int64_t)ta * n] = -acc0;
+  if (ta + 1 < bb) Lbuf[(int64_t)i + (int64_t)(ta + 1) * n] = -acc1;
+}
+
+// W[i, k0 + t] = L[i, t] for the rows pivoted before the panel (the fix-up's results).
+__global__ void fixup_store_kernel(int n, int k0, int bb, double* __restrict__ W, const int* __restrict__ posrow,
+                                   const double* __restrict__ Lbuf, const int32_t* status) {
+  if (*status != GJ_OK || k0 == 0) return;
+  const int64_t total = (int64_t)n * bb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / n), i = (int)(e - (int64_t)t * n);
+    if (posrow[i] < k0) W[(int64_t)i + (int64_t)(k0 + t) * n] = Lbuf[e];
   }
 }
 
@@ -946,9 +957,13 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
       }
       if (k0 > 0) {
         ProfScope ps(st_, "fixup_used_rows", 2.0 * k0 * (double)bb * bb, 16.0 * k0 * (double)bb);
-        fixup_used_rows_kernel<<<(n + 31) / 32, 256, 0, st_>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
+        const dim3 fx_grid((n + kFixRows - 1) / kFixRows, (bb + kFixCols - 1) / kFixCols);
+        fixup_used_rows_kernel<<<fx_grid, 256, 0, st_>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
         GJ_CUDA(cudaGetLastError());
-        prof_count(1);
+        fixup_store_kernel<<<(unsigned)std::min<int64_t>(((int64_t)n * bb + 255) / 256, sms * 8), 256, 0, st_>>>(
+            n, k0, bb, W, posrow, Lbuf, out.status);
+        GJ_CUDA(cudaGetLastError());
+        prof_count(2);
       }
       if (BB > bb) {  // the rest of the outer panel
         gj_status st;
@@ -1006,9 +1021,9 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
     cudaStream_t sb = se.sb;
     GJ_CUDA(cudaEventRecord(se.ev_a, s));  // set-up done
     GJ_CUDA(cudaStreamWaitEvent(sb, se.ev_a, 0));
-    // SMs left to sb: the cluster's plus room for its fix-ups and narrow updates (four
-    // cluster sizes measured best at n = 8192: the panel stream is the longer one)
-    const int wide_ctas = std::max(1, sms - std::min(4 * cs, sms / 2));
+    // SMs left to sb: the cluster's plus room for its fix-ups and narrow updates (3.5
+    // cluster sizes measured best at n = 8192, the two streams then take about as long)
+    const int wide_ctas = std::max(1, sms - std::min((7 * cs) / 2, sms / 2));
     struct Pending {
       bool valid = false;
       int K0 = 0, BB = 0, skip = 0;
