@@ -8,8 +8,12 @@ determinant) with the input already resident in device memory.  The metric is in
 GFLOP/s counted as 2 n^3 per inverse.
 
 Other workloads (``--workload``): ``inv128`` (one 128 x 128 N(0,1) matrix, full pivoting)
-and ``batch200k`` (200,000 matrices, orders uniform in 4..64, diagonally dominant,
-partial pivoting, one persistent launch replayed as a CUDA graph; metric matrices/s).
+``batch200k`` (200,000 matrices, orders uniform in 4..64, diagonally dominant,
+partial pivoting, one persistent launch replayed as a CUDA graph; metric matrices/s),
+``mixed16384`` (one 16384 x 16384 FP32 matrix, kappa 1e6: reduced-precision GJ plus
+Newton-Schulz refinement to a 1e-12 normalised residual) and ``mixedbatch4096`` (4,096
+FP32 matrices, orders uniform in 128..1024, kappa log-uniform in 1e2..1e8, each refined to
+a 1e-12 normalised residual by a pool of host workers with one stream each).
 
 ``--impl reference`` times the CPU oracle (plain FP64 C, the test reference) on the host
 cores on a bounded sample of the same workload and prints the same JSON line.
@@ -61,7 +65,31 @@ WORKLOADS = {
                       name="gj-batched-200k-n4to64-fp64-partial"),
     "mixed16384": dict(n=16384, kappa=1e6, pivot=1, seed=wl.SEED_BASE + 4,
                        name="gj-inverse-16384-fp32in-mixed-refined"),
+    "mixedbatch4096": dict(count=4096, seed=wl.SEED_BASE + 5, pivot=1,
+                           name="gj-batched-mixed-4096-n128to1024-fp32in-refined"),
 }
+
+_MIXED_BATCH_HOST = {}
+_MIXED_BATCH_DEV = {}
+
+
+def mixed_batch_on_device(count: int, seed: int, dev):
+    """The batched mixed recipe generated on the GPU (cached: the QRs take a while)."""
+    key = (count, seed, str(dev))
+    if key not in _MIXED_BATCH_DEV:
+        sizes, kappas, offsets = wl.mixed_batch_params(count, seed)
+        _MIXED_BATCH_DEV[key] = (sizes, offsets, wl.mixed_batch_device(sizes, kappas, offsets, seed, device=dev))
+    return _MIXED_BATCH_DEV[key]
+
+
+def mixed_batch_sample(count: int, seed: int):
+    """The first ``count`` matrices of the batched mixed recipe (host generator), cached."""
+    key = (count, seed)
+    if key not in _MIXED_BATCH_HOST:
+        sizes, kappas, offsets = wl.mixed_batch_params(count, seed)
+        packed32 = wl.mixed_batch_host(sizes, kappas, offsets, seed)
+        _MIXED_BATCH_HOST[key] = (sizes, offsets, packed32.astype(np.float64))
+    return _MIXED_BATCH_HOST[key]
 
 
 # ----------------------------------------------------------------- distributed helpers
@@ -178,8 +206,10 @@ def roofline_tensor(tensor_tflops: float, fp64_equiv_tflops: float, pairs: int, 
     return {"bound": "tensor", "achieved": round(tensor_tflops, 2), "peak": peak, "unit": "TFLOP/s",
             "frac": round(tensor_tflops / peak, 4), "traffic": traffic,
             "peak_source": f"BF16 dense sustained {src} (kernel timed inside a long step)",
-            "work": f"{pairs} BF16 digit-slice products per FP64 product term (2 K FLOP each per element)",
-            "fp64_equivalent_tflops": round(fp64_equiv_tflops, 3)}
+            "work": (f"{pairs} BF16 digit-slice products per FP64 product term (2 K FLOP each per element)" if pairs
+                     else "BF16 digit-slice products, S (S + 1) / 2 per FP64 product term, S per call (X0, residual, "
+                          "correction slices)"),
+            "fp64_equivalent_tflops": round(fp64_equiv_tflops, 3) if fp64_equiv_tflops is not None else None}
 
 
 def roofline_fp64(achieved_gflops: float, traffic) -> dict:
@@ -208,6 +238,20 @@ def cpu_oracle_sample(workload: str, repeat: int = 1) -> dict:
         return {"value": take / dt, "unit": "matrices/s", "cores": cores, "kind": "oracle",
                 "sample": f"first {take} of the 200000 matrices, oracle over {cores} threads",
                 "gflops": float((2.0 * sizes.astype(np.float64) ** 3).sum() / dt / 1e9)}
+    if workload == "mixedbatch4096":
+        # the same recipe's first 192 matrices (orders 128..1024, kappa 1e2..1e8, the FP32
+        # values converted exactly), plain FP64 Gauss-Jordan over all host cores
+        take = 192
+        sizes, offsets, packed = mixed_batch_sample(take, W["seed"])
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        for _ in range(repeat):
+            oracle.invert_many(sizes, packed, offsets, W["pivot"], threads=cores)
+        dt = (time.perf_counter() - t0) / repeat
+        return {"value": float((2.0 * sizes.astype(np.float64) ** 3).sum() / dt / 1e9), "unit": "GFLOP/s",
+                "cores": cores, "kind": "oracle",
+                "sample": f"first {take} of the 4096 matrices (host generator), FP64 oracle over {cores} threads",
+                "matrices_per_s": take / dt}
     if workload == "mixed16384":
         n = 1536
         A = wl.svd_conditioned(n, W["kappa"], W["seed"], dtype=np.float32).astype(np.float64)
@@ -327,6 +371,28 @@ def run_gpu(args) -> None:
         dominant = "update_ozaki_tc"
         h2d = 4 * n * n
         d2h = 8 * n * n
+    elif args.workload == "mixedbatch4096":
+        t_gen = time.perf_counter()
+        sizes, offsets, flatA = mixed_batch_on_device(W["count"], W["seed"] + rank, dev)
+        torch.cuda.synchronize(dev)
+        extra["input_generation_s"] = round(time.perf_counter() - t_gen, 1)
+        flatX = torch.empty(flatA.numel(), dtype=torch.float64, device=dev)
+        As = [wl.matrix_view(flatA, int(n), int(o)) for n, o in zip(sizes, offsets)]
+        Xs = [wl.matrix_view(flatX, int(n), int(o)) for n, o in zip(sizes, offsets)]
+        flops_step = float((2.0 * sizes.astype(np.float64) ** 3).sum())
+        units_step = len(sizes)
+        mixed_state = {}
+
+        def step():
+            r = gj.invert_mixed_batched(As, Xs, x0_slices=args.x0_slices, corr_slices=4, tol=1e-12, max_iter=10,
+                                        workers=args.workers, stream=stream)
+            if r["status"] != 0:
+                raise RuntimeError(f"gj_invert_mixed_batched: {gj.status_string(r['status'])}")
+            mixed_state.update(r)
+
+        dominant = "update_ozaki_tc"
+        h2d = 4 * flatA.numel()
+        d2h = 8 * flatX.numel()
     else:
         n = W["n"]
         A = wl.gaussian(n, W["seed"] + rank, shift=W["shift"] * n)
@@ -387,6 +453,10 @@ def run_gpu(args) -> None:
         value = total_units / (ms_max / 1000.0)
         unit = "matrices/s"
         extra["gflops"] = total_flops / (ms_max / 1000.0) / 1e9
+    elif args.workload == "mixedbatch4096":
+        value = total_flops / (ms_max / 1000.0) / 1e9
+        unit = "GFLOP/s"
+        extra["matrices_per_s"] = total_units / (ms_max / 1000.0)
     else:
         value = total_flops / (ms_max / 1000.0) / 1e9
         unit = "GFLOP/s"
@@ -399,19 +469,24 @@ def run_gpu(args) -> None:
     if dominant in ("update_ozaki_wide", "update_ozaki_tc"):
         d = prof[dominant]
         avg_ms = d["total_ms"] / d["launches"]
-        S = args.slices or 8
-        pairs = S * (S + 1) // 2
-        fp64_fl = d["flops"] / d["launches"]
+        # the profile counts tensor FLOP (S (S + 1) / 2 slice products per FP64 term); the
+        # mixed paths run the update with several slice counts, so no single FP64 equivalent
+        S = None if args.workload in ("mixed16384", "mixedbatch4096") else (args.slices or 8)
+        pairs = S * (S + 1) // 2 if S else None
+        tc_fl = d["flops"] / d["launches"]
         t = NCU_TRAFFIC.get(dominant)
         traffic = args.traffic
         if traffic is None and t and "n" in W:
             traffic = t["bytes"] * (W["n"] / t["n"]) ** 2
-        roof = roofline_tensor(pairs * fp64_fl / (avg_ms / 1000.0) / 1e12, fp64_fl / (avg_ms / 1000.0) / 1e12, pairs,
-                               traffic)
+        tensor_tflops = tc_fl / (avg_ms / 1000.0) / 1e12
+        roof = roofline_tensor(tensor_tflops, tensor_tflops / pairs if pairs else None, pairs, traffic)
         roof["kernel"] = dominant
         roof["avg_launch_ms"] = round(avg_ms, 6)
         roof["share_of_step"] = round(d["total_ms"] / ms, 4)
-        if dominant == "update_ozaki_wide" and W["n"] >= 2048:
+        if args.workload == "mixedbatch4096":
+            roof["note"] = ("launches of all worker streams; they overlap, so share_of_step sums overlapped "
+                            "time and avg_launch_ms includes time shared with other streams' kernels")
+        if dominant == "update_ozaki_wide" and W.get("n", 0) >= 2048:
             cs = min(16, -(-W["n"] // 256))
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
             roof["grid_sms"] = sms - min((7 * cs) // 2, sms // 2)
@@ -433,6 +508,13 @@ def run_gpu(args) -> None:
         roof["avg_launch_ms"] = round(avg_ms, 6)
         roof["share_of_step"] = round(d["total_ms"] / ms, 4)
 
+    if args.workload == "mixedbatch4096":
+        rung = np.asarray(mixed_state["rung"])
+        its = np.asarray(mixed_state["iters"])
+        extra["resid_max"] = float(np.max(mixed_state["resid"]))
+        extra["x0_rung_counts"] = {f"{sl}_slices": int((rung == i).sum())
+                                   for i, sl in enumerate([args.x0_slices, max(args.x0_slices, 5), 8])}
+        extra["refinement_steps_mean"] = round(float(its.mean()), 3)
     if args.workload == "mixed16384":
         n = W["n"]
         extra["resid"] = mixed_state.get("resid")
@@ -484,6 +566,13 @@ def run_gpu(args) -> None:
                         "input": "U diag(sigma) V^T, Haar U,V, sigma log-spaced 1..1e6, FP32, seed 1405 (GPU QR)",
                         "method": "reduced-precision blocked GJ (tensor update, x0 slices) + Newton-Schulz, "
                                   "FP64-level residual"})
+        elif args.workload == "mixedbatch4096":
+            cfg.update({"count": W["count"], "orders": "U{128..1024}", "kappa": "logU[1e2, 1e8]", "tol": 1e-12,
+                        "input": "U diag(sigma) V^T, Haar U,V (GPU QR), sigma log-spaced 1..kappa, FP32, seed 1406",
+                        "method": "per matrix: reduced-precision blocked GJ (tensor update, x0 slices) + "
+                                  "Newton-Schulz, FP64-level residual, ladder 3 -> 5 -> 8 slices",
+                        "launch": f"host worker pool, {args.workers or 8} streams, largest first",
+                        "x0_slices": args.x0_slices})
         elif args.workload == "inv128":
             cfg.update({"n": W["n"], "input": "N(0,1), seed 1402",
                         "kernel": "one 16-CTA cluster, rows spread over its CTAs (FP64 of 16 SMs)"})
@@ -517,6 +606,8 @@ def run_e2e(args, gj, L, W, stream, dev, h2d, d2h, units_step, flops_step, rank)
     import ctypes
     import torch
     steps = max(1, min(args.steps, 3)) if args.workload in ("inv8192", "mixed16384") else args.steps
+    if args.workload == "mixedbatch4096":
+        steps = 1
     if args.workload == "mixed16384":
         n = W["n"]
         hA = wl.svd_conditioned_device(n, W["kappa"], W["seed"] + rank, device=dev).cpu().pin_memory()
@@ -560,24 +651,24 @@ def run_e2e(args, gj, L, W, stream, dev, h2d, d2h, units_step, flops_step, rank)
                 h_sg.copy_(sg, non_blocking=True)
                 h_lg.copy_(lg, non_blocking=True)
             stream.synchronize()
-    elif args.workload == "mixed16384":
-        n = W["n"]
-        dA32 = wl.svd_conditioned_device(n, W["kappa"], W["seed"] + rank, device=dev)
-        dX = torch.empty((n, n), dtype=torch.float64, device=dev).t().contiguous().t()
-        flops_step = 2.0 * n ** 3
-        units_step = 1
-        mixed_state = {}
+    elif args.workload == "mixedbatch4096":
+        sizes, offsets, flatA = mixed_batch_on_device(W["count"], W["seed"] + rank, dev)
+        hA = flatA.cpu().pin_memory()
+        hX = torch.empty(hA.numel(), dtype=torch.float64).pin_memory()
+        dA = torch.empty(hA.numel(), dtype=torch.float32, device=dev)
+        dX = torch.empty(hA.numel(), dtype=torch.float64, device=dev)
+        As = [wl.matrix_view(dA, int(n), int(o)) for n, o in zip(sizes, offsets)]
+        Xs = [wl.matrix_view(dX, int(n), int(o)) for n, o in zip(sizes, offsets)]
 
-        def step():
-            r = gj.invert_mixed(dA32, out=dX, x0_slices=args.x0_slices, corr_slices=4, tol=1e-12, max_iter=10,
-                                stream=stream)
-            if r["status"] != 0:
-                raise RuntimeError(f"gj_invert_mixed: {gj.status_string(r['status'])}")
-            mixed_state.update(r)
-
-        dominant = "update_ozaki_tc"
-        h2d = 4 * n * n
-        d2h = 8 * n * n
+        def one():
+            with torch.cuda.stream(stream):
+                dA.copy_(hA, non_blocking=True)
+                r = gj.invert_mixed_batched(As, Xs, x0_slices=args.x0_slices, corr_slices=4, tol=1e-12,
+                                            max_iter=10, workers=args.workers, stream=stream)
+                if r["status"] != 0:
+                    raise RuntimeError(gj.status_string(r["status"]))
+                hX.copy_(dX, non_blocking=True)
+            stream.synchronize()
     else:
         n = W["n"]
         A = wl.gaussian(n, W["seed"] + rank, shift=W["shift"] * n)
@@ -620,6 +711,7 @@ def main():
     ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
     ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 8)")
     ap.add_argument("--x0-slices", type=int, default=3, help="digit slices of the mixed path's first inverse")
+    ap.add_argument("--workers", type=int, default=8, help="mixedbatch4096: host workers (= streams)")
     ap.add_argument("--compare-fma", action="store_true", help="mixed workload: also time the FP64-FMA update GJ")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")

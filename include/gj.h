@@ -231,6 +231,32 @@ gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, double* X, int
                           double tol, int max_iter, double* resid_out, int* iters_out, int* rung_out, int* det_sign,
                           double* det_log2, void* stream);
 
+/*
+ * gj_invert_mixed_batched -- gj_invert_mixed over a batch of FP32 matrices of different
+ * orders (not in the paper: batching and the precision ladder are outside its method).
+ * A pool of host workers, each with its own CUDA stream and workspace, takes the
+ * matrices largest first; each matrix climbs its own ladder from its own residuals.
+ *   count      number of matrices (>= 0).
+ *   n, lda     [count] host arrays: order (>= 0) and leading dimension (>= max(1, n)).
+ *   A          [count] host array of device pointers: FP32 column-major matrices.
+ *   X          [count] host array of device pointers: FP64 outputs, leading dimension n.
+ *              A and X of different matrices must not overlap.
+ *   x0_slices, corr_slices, tol, max_iter   as gj_invert_mixed, for every matrix.
+ *   workers    host workers (= concurrent streams), 0..64; 0 chooses min(count, 8).
+ *   status     [count] host out (may be NULL): gj_invert_mixed's status per matrix.
+ *   resid, iters, rung, det_sign, det_log2   [count] host outs (may be NULL): per-matrix
+ *              values of gj_invert_mixed's outputs.
+ *   stream     the batch starts after the work queued on it before the call.
+ * Returns GJ_ERR_ARG (nothing launched) for a bad count, order, leading dimension, null
+ * pointer of a non-empty matrix or option; otherwise the first negative per-matrix status in
+ * matrix order, else the first non-OK one (e.g. GJ_NOT_CONVERGED), else GJ_OK.
+ * Synchronous.  Workspace: gj_invert_mixed's, per worker, for the matrix it holds.
+ */
+gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, const int32_t* lda, const float* const* A,
+                                  double* const* X, int x0_slices, int corr_slices, double tol, int max_iter,
+                                  int workers, int32_t* status, double* resid, int32_t* iters, int32_t* rung,
+                                  int8_t* det_sign, double* det_log2, void* stream);
+
 /* A batched plan fixes the orders (host copy given at creation), precomputes the
  * largest-first work order and launch shape, and can be replayed as a CUDA graph. */
 typedef struct gj_plan gj_plan;

@@ -70,6 +70,8 @@ def lib() -> ctypes.CDLL:
     L.gj_gemm_update_emulated.argtypes = [I64, I64, I64, P, I64, P, I64, P, I64, I, P]
     L.gj_invert_mixed.restype = I
     L.gj_invert_mixed.argtypes = [I64, P, I64, P, I, I, D, I, P, P, P, P, P, P]
+    L.gj_invert_mixed_batched.restype = I
+    L.gj_invert_mixed_batched.argtypes = [I64, P, P, P, P, I, I, D, I, I, P, P, P, P, P, P, P]
     L.gj_batched_plan_create.restype = I
     L.gj_batched_plan_create.argtypes = [ctypes.POINTER(P), I64, P, I]
     L.gj_batched_plan_create_ex.restype = I
@@ -307,6 +309,51 @@ def invert_mixed(A32, out=None, *, x0_slices: int = 3, corr_slices: int = 4, tol
         raise GJError(st, "gj_invert_mixed")
     return {"X": out, "status": st, "resid": r.value, "iters": it.value, "rung": rg.value, "det_sign": sg.value,
             "det_log2": lg.value}
+
+
+def invert_mixed_batched(As, Xs=None, *, x0_slices: int = 3, corr_slices: int = 4, tol: float = 1e-12,
+                         max_iter: int = 10, workers: int = 0, stream=None) -> dict:
+    """``gj_invert_mixed_batched``: a list of square FP32 column-major device matrices -> their FP64
+    inverses (``Xs``, allocated when not given).  Returns a dict with ``X`` (the list), the call's
+    ``status`` and per-matrix numpy arrays ``statuses``, ``resid``, ``iters``, ``rung``,
+    ``det_sign``, ``det_log2``."""
+    import numpy as np
+    import torch
+    L = lib()
+    count = len(As)
+    ns = np.zeros(max(1, count), dtype=np.int32)
+    lds = np.ones(max(1, count), dtype=np.int32)
+    if Xs is None:
+        Xs = [torch.empty((int(a.shape[0]), int(a.shape[0])), dtype=torch.float64, device=a.device).t().contiguous().t()
+              for a in As]
+    if len(Xs) != count:
+        raise ValueError("As and Xs differ in length")
+    for m, (a, x) in enumerate(zip(As, Xs)):
+        if a.ndim != 2 or a.shape[0] != a.shape[1] or str(a.dtype) != "torch.float32":
+            raise ValueError("square float32 torch tensors expected")
+        n = int(a.shape[0])
+        if n > 1 and (a.stride(0) != 1 or a.stride(1) < n):
+            raise ValueError("matrices must be column-major")
+        if tuple(x.shape) != (n, n) or str(x.dtype) != "torch.float64" or (n > 1 and x.stride() != (1, n)):
+            raise ValueError("outputs must be column-major float64 (n, n) with leading dimension n")
+        ns[m] = n
+        lds[m] = max(1, int(a.stride(1)) if n > 1 else 1)
+    pa = np.array([_ptr(a) for a in As] or [0], dtype=np.uint64)
+    px = np.array([_ptr(x) for x in Xs] or [0], dtype=np.uint64)
+    st = np.zeros(max(1, count), dtype=np.int32)
+    rs = np.zeros(max(1, count), dtype=np.float64)
+    it = np.zeros(max(1, count), dtype=np.int32)
+    rg = np.zeros(max(1, count), dtype=np.int32)
+    sg = np.zeros(max(1, count), dtype=np.int8)
+    lg = np.zeros(max(1, count), dtype=np.float64)
+    r = L.gj_invert_mixed_batched(count, ns.ctypes.data, lds.ctypes.data, pa.ctypes.data, px.ctypes.data,
+                                  int(x0_slices), int(corr_slices), float(tol), int(max_iter), int(workers),
+                                  st.ctypes.data, rs.ctypes.data, it.ctypes.data, rg.ctypes.data, sg.ctypes.data,
+                                  lg.ctypes.data, _stream_handle(stream))
+    if r < 0:
+        raise GJError(r, "gj_invert_mixed_batched")
+    return {"X": Xs, "status": r, "statuses": st[:count], "resid": rs[:count], "iters": it[:count],
+            "rung": rg[:count], "det_sign": sg[:count], "det_log2": lg[:count]}
 
 
 def invert_batched(n_dev, A_ptrs, X_ptrs, status, det_sign=None, det_log2=None, *, pivot_mode: int = PIVOT_PARTIAL,

@@ -615,7 +615,8 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   if (ntiles <= 0) return GJ_OK;
   const int grid = std::min(ntiles, (max_ctas > 0 && max_ctas < sms) ? max_ctas : sms);
   {
-    ProfScope ps(s, prof_name, 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
+    // tensor FLOP: S (S + 1) / 2 digit-slice products per FP64 product term
+    ProfScope ps(s, prof_name, 0.5 * S * (S + 1) * 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
                  16.0 * (double)M * (double)N);
     ozaki_update_kernel<<<grid, kThreads, smem, s>>>(mapA, mapB, (int)M, (int)N, (int)mpad, (int)npad, S, nkc,
                                                     tiles_m, tiles_n, ts_lo, ts_hi, zero_lo, zero_hi, C, ldc, erow,

@@ -13,7 +13,9 @@ Workload shapes:
   * one large n x n matrix N(0,1) + 0.1 n I (8192 x 8192, partial pivoting, blocked);
   * a batch of matrices with orders drawn uniformly from 4..64, entries U[-1,1],
     each diagonal entry set to 1 + sum of the absolute off-diagonal entries of its row;
-  * U diag(sigma) V^T with Haar U, V and log-spaced sigma (mixed precision).
+  * U diag(sigma) V^T with Haar U, V and log-spaced sigma (mixed precision);
+  * a batch of such matrices, orders uniform in 128..1024, condition numbers
+    log-uniform in [1e2, 1e8] (batched mixed precision).
 """
 from __future__ import annotations
 
@@ -117,3 +119,55 @@ def svd_conditioned_device(n: int, kappa: float, seed: int, device="cuda"):
     sigma = torch.logspace(0.0, float(np.log10(kappa)), n, device=device, dtype=torch.float32)
     A = (U * sigma[None, :]) @ V.T
     return A.t().contiguous().t()
+
+
+def mixed_batch_params(count: int, seed: int, n_min: int = 128, n_max: int = 1024, kappa_min: float = 1e2,
+                       kappa_max: float = 1e8):
+    """Orders uniform in ``n_min..n_max`` (inclusive) and condition numbers log-uniform in
+    ``[kappa_min, kappa_max]`` for a batch of U diag(sigma) V^T matrices.  Returns
+    ``(sizes[int32], kappas[float64], offsets[int64])``; matrix m occupies
+    ``offsets[m] : offsets[m] + sizes[m]**2`` of a packed column-major buffer."""
+    g = rng(seed)
+    sizes = g.integers(n_min, n_max + 1, size=count, dtype=np.int64).astype(np.int32)
+    kappas = 10.0 ** g.uniform(np.log10(kappa_min), np.log10(kappa_max), size=count)
+    sq = sizes.astype(np.int64) ** 2
+    offsets = np.zeros(count, dtype=np.int64)
+    if count > 1:
+        offsets[1:] = np.cumsum(sq)[:-1]
+    return sizes, kappas, offsets
+
+
+def mixed_batch_seed(seed: int, m: int) -> int:
+    """Seed of matrix m of a mixed batch drawn with ``seed``."""
+    return seed * 100003 + m
+
+
+def mixed_batch_host(sizes: np.ndarray, kappas: np.ndarray, offsets: np.ndarray, seed: int) -> np.ndarray:
+    """Packed FP32 buffer of the batch: matrix m is ``svd_conditioned`` of its order and kappa
+    with seed ``mixed_batch_seed(seed, m)``."""
+    total = int(offsets[-1] + int(sizes[-1]) ** 2) if len(sizes) else 0
+    packed = np.empty(total, dtype=np.float32)
+    for m, (n, k) in enumerate(zip(sizes, kappas)):
+        n = int(n)
+        A = svd_conditioned(n, float(k), mixed_batch_seed(seed, m), dtype=np.float32)
+        packed[offsets[m]: offsets[m] + n * n] = A.reshape(-1, order="F")
+    return packed
+
+
+def mixed_batch_device(sizes: np.ndarray, kappas: np.ndarray, offsets: np.ndarray, seed: int, device="cuda"):
+    """Packed FP32 device buffer of the batch: matrix m is ``svd_conditioned_device`` of its
+    order and kappa with seed ``mixed_batch_seed(seed, m)`` (the GPU's generator, so not the
+    same numbers as ``mixed_batch_host``)."""
+    import torch
+    total = int(offsets[-1] + int(sizes[-1]) ** 2) if len(sizes) else 0
+    flat = torch.empty(total, dtype=torch.float32, device=device)
+    for m, (n, k) in enumerate(zip(sizes, kappas)):
+        n = int(n)
+        A = svd_conditioned_device(n, float(k), mixed_batch_seed(seed, m), device=device)
+        matrix_view(flat, n, int(offsets[m])).copy_(A)
+    return flat
+
+
+def matrix_view(flat, n: int, offset: int):
+    """Column-major (n, n) view of ``flat[offset : offset + n * n]`` (torch tensor)."""
+    return flat[offset: offset + n * n].view(n, n).t()

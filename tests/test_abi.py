@@ -34,7 +34,8 @@ def lib():
 
 def test_header_declares_entry_points():
     names = _declared_functions()
-    for must in ("gj_invert", "gj_invert_ex", "gj_solve", "gj_solve_ex", "gj_invert_batched", "gj_invert_batched_noalloc", "gj_batched_plan_create",
+    for must in ("gj_invert", "gj_invert_ex", "gj_solve", "gj_solve_ex", "gj_invert_batched", "gj_invert_batched_noalloc",
+                 "gj_invert_mixed", "gj_invert_mixed_batched", "gj_batched_plan_create",
                  "gj_batched_plan_execute", "gj_batched_plan_destroy", "gj_status_string"):
         assert must in names
 
@@ -82,6 +83,28 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.gj_invert_mixed(4, p, 4, p, 3, 4, 0.0, 5, None, None, None, None, None, None) == gj.ERR_ARG
     assert L.gj_invert_mixed(4, p, 3, p, 3, 4, 1e-12, 5, None, None, None, None, None, None) == gj.ERR_ARG
     assert L.gj_invert_mixed(0, None, 1, None, 3, 4, 1e-12, 5, None, None, None, None, None, None) == gj.OK
+    # batched mixed: every argument is checked before the device is touched
+    ns = np.array([4, 0, 5], dtype=np.int32)
+    lds = np.array([4, 1, 5], dtype=np.int32)
+    ptrs = np.array([p, 0, p], dtype=np.uint64)
+    nul = np.array([p, 0, 0], dtype=np.uint64)
+
+    def mb(count=3, n=ns, ld=lds, a=ptrs, x=ptrs, x0=3, corr=4, tol=1e-12, it=5, workers=0):
+        return L.gj_invert_mixed_batched(count, n.ctypes.data if n is not None else None,
+                                         ld.ctypes.data if ld is not None else None,
+                                         a.ctypes.data if a is not None else None,
+                                         x.ctypes.data if x is not None else None, x0, corr, tol, it, workers,
+                                         None, None, None, None, None, None, None)
+    assert mb(count=-1) == gj.ERR_ARG
+    assert mb(x0=0) == gj.ERR_ARG and mb(corr=9) == gj.ERR_ARG
+    assert mb(tol=0.0) == gj.ERR_ARG and mb(it=-1) == gj.ERR_ARG
+    assert mb(workers=65) == gj.ERR_ARG and mb(workers=-1) == gj.ERR_ARG
+    assert mb(n=None) == gj.ERR_ARG and mb(a=None) == gj.ERR_ARG
+    assert mb(ld=np.array([3, 1, 5], dtype=np.int32)) == gj.ERR_ARG          # lda < n
+    assert mb(ld=np.array([4, 0, 5], dtype=np.int32)) == gj.ERR_ARG          # lda < 1 for n == 0
+    assert mb(n=np.array([4, -1, 5], dtype=np.int32)) == gj.ERR_ARG
+    assert mb(x=nul) == gj.ERR_ARG                                           # null X of a non-empty matrix
+    assert mb(count=0, n=None, ld=None, a=None, x=None) == gj.OK
     # solve: negative sizes, leading dimensions below n, bad mode, null pointers, the
     # single-CTA path (no right-hand sides there); n == 0 is the empty product
     assert L.gj_solve(-1, 1, p, 1, p, 1, p, 1, 1, None, None) == gj.ERR_ARG
