@@ -900,7 +900,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
     GJ_CUDA(cudaGetLastError());
   }
 
-  GJ_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GJ_CUDA(allow_max_dynamic_smem((const void*)panel_kernel));
   if (cs > 8) GJ_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

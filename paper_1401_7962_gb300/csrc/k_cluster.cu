@@ -350,7 +350,7 @@ gj_status launch_cluster_single(int n, const double* A, int64_t lda, double* X, 
   if (n < 1 || n > kCtaMaxN) return GJ_ERR_ARG;
   int cs = (n >= 96) ? 16 : (n >= 48 ? 8 : 4);
   const size_t smem = clu_smem_bytes(n, cs);
-  GJ_CUDA(cudaFuncSetAttribute(cluster_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GJ_CUDA(allow_max_dynamic_smem((const void*)cluster_inv_kernel));
   if (cs > 8) GJ_CUDA(cudaFuncSetAttribute(cluster_inv_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

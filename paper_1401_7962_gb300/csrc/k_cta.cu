@@ -460,7 +460,7 @@ gj_status launch_batched_nt(int64_t q_begin, int64_t q_end, int nmax, const int3
                             const CtaOut& out, cudaStream_t s) {
   const size_t smem = cta_smem_bytes(nmax);
   auto kern = cta_batched_kernel<NT>;
-  GJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GJ_CUDA(allow_max_dynamic_smem((const void*)kern));
   int dev = 0, sms = 0, per_sm = 0;
   GJ_CUDA(cudaGetDevice(&dev));
   GJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -508,13 +508,13 @@ gj_status launch_cta_single(int n, const double* A, int64_t lda, double* X, int 
   prof_count(1);
   ProfScope ps(s, "cta_single", 2.0 * n * n * (double)n, 16.0 * n * n);
   if (n > 64) {
-    GJ_CUDA(cudaFuncSetAttribute(cta_single_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GJ_CUDA(allow_max_dynamic_smem((const void*)cta_single_kernel<512>));
     cta_single_kernel<512><<<1, 512, smem, s>>>(n, A, lda, X, pivot_mode, tau, out);
   } else if (n > 32) {
-    GJ_CUDA(cudaFuncSetAttribute(cta_single_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GJ_CUDA(allow_max_dynamic_smem((const void*)cta_single_kernel<256>));
     cta_single_kernel<256><<<1, 256, smem, s>>>(n, A, lda, X, pivot_mode, tau, out);
   } else {
-    GJ_CUDA(cudaFuncSetAttribute(cta_single_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GJ_CUDA(allow_max_dynamic_smem((const void*)cta_single_kernel<128>));
     cta_single_kernel<128><<<1, 128, smem, s>>>(n, A, lda, X, pivot_mode, tau, out);
   }
   GJ_CUDA(cudaGetLastError());

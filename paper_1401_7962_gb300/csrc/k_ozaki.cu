@@ -600,7 +600,7 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   st = make_slice_map(&mapB, Bs, (int64_t)S * npad, kTN);
   if (st != GJ_OK) return st;
   const size_t smem = SmemLayout::bytes(S);
-  GJ_CUDA(cudaFuncSetAttribute(ozaki_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GJ_CUDA(allow_max_dynamic_smem((const void*)ozaki_update_kernel));
   const int nkc = (K + kKC - 1) / kKC;
   const int tiles_m = (int)((M + kTM - 1) / kTM), tiles_n = (int)((N + kTN - 1) / kTN);
   // column tiles lying wholly inside [zero_lo, zero_hi) receive nothing: not scheduled

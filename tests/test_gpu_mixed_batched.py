@@ -83,10 +83,11 @@ def test_batch_equals_single_matrix_calls():
 
 
 def test_each_matrix_climbs_its_own_ladder():
-    """1-slice X0: the kappa = 1e2 matrix converges on the first rung, the kappa = 1e6 one
-    must climb (2^-7 kappa >> 1), in the same batch."""
+    """3-slice X0 (update truncation about 5 128 2^-21 of the scales per panel): the
+    kappa = 1e2 matrix contracts on the first rung, the kappa = 1e6 one cannot and climbs,
+    in the same batch."""
     host, dev, _ = _batch([400, 400], [1e2, 1e6], seed=4300)
-    r = gj.invert_mixed_batched(dev, x0_slices=1, corr_slices=4, tol=1e-12, workers=2)
+    r = gj.invert_mixed_batched(dev, x0_slices=3, corr_slices=4, tol=1e-12, workers=2)
     assert r["status"] == gj.OK
     assert r["rung"][0] == 0 and r["rung"][1] >= 1
     for m in range(2):
