@@ -9,6 +9,7 @@
 #include <numeric>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "gj_internal.cuh"
@@ -51,6 +52,27 @@ cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t s) {
     pool = g_pools[dev];
   }
   return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+namespace {
+std::mutex g_smem_mu;
+std::vector<std::pair<const void*, int>> g_smem_done;  // (kernel, device) pairs already raised
+}  // namespace
+
+cudaError_t allow_max_dynamic_smem(const void* func) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  for (const auto& d : g_smem_done)
+    if (d.first == func && d.second == dev) return cudaSuccess;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess) return e;
+  int optin = 0;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) g_smem_done.emplace_back(func, dev);
+  return e;
 }
 
 gj_status cuda_fail(cudaError_t e, const char* what) {

@@ -23,19 +23,12 @@ void set_last_error(const char* msg);
   } while (0)
 
 // Raise a kernel's dynamic shared memory cap to the device's opt-in maximum (less its
-// static shared memory).  The cap is one value per function for the whole process: a
-// call that lowered it to its own need could make a concurrent call's larger launch (on
-// another host thread) fail, so every launch site sets the same, largest value.  The cap
-// only bounds what a launch may request; occupancy follows the bytes each launch asks for.
-inline cudaError_t allow_max_dynamic_smem(const void* func) {
-  cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, func);
-  if (e != cudaSuccess) return e;
-  int dev = 0, optin = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-}
+// static shared memory), once per kernel and device.  The cap is one value per function for
+// the whole process: a call that lowered it to its own need could make a concurrent call's
+// larger launch (on another host thread) fail, so every launch site sets the same, largest
+// value.  The cap only bounds what a launch may request; occupancy follows the bytes each
+// launch asks for.
+cudaError_t allow_max_dynamic_smem(const void* func);
 
 // ----------------------------------------------------------------- profiling
 

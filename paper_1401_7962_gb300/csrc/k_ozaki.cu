@@ -103,13 +103,10 @@ __device__ __forceinline__ void write_digits(__nv_bfloat16* out, int S, int64_t 
 // Rows of L (M x K, column-major, ld ldl) -> slices [S][mpad][128] and row exponents.
 // minus_one_at[k] (optional): subtract 1 from L[minus_one_at[k], k] (the blocked
 // Gauss-Jordan L of the panel: pivot entries minus the identity).
-__global__ void slice_rows_kernel(int M, int K, const double* __restrict__ L, int64_t ldl,
-                                  const int* __restrict__ minus_one_at, int S, int mpad,
-                                  __nv_bfloat16* __restrict__ out, int* __restrict__ erow, const int32_t* status) {
-  if (status && *status != GJ_OK) return;
+__device__ __forceinline__ void slice_rows(int warp, int nwarps, int M, int K, const double* __restrict__ L,
+                                           int64_t ldl, const int* __restrict__ minus_one_at, int S, int mpad,
+                                           __nv_bfloat16* __restrict__ out, int* __restrict__ erow) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   int mo[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -137,13 +134,11 @@ __global__ void slice_rows_kernel(int M, int K, const double* __restrict__ L, in
 // Columns of U (K x N) -> slices [S][npad][128] and column exponents.  U[k, j] is
 // U[k + j*ldu], or, with row_ids, W[row_ids[k] + j*ldu] (the pivot rows of a panel);
 // columns in [zero_lo, zero_hi) are zero.
-__global__ void slice_cols_kernel(int N, int K, const double* __restrict__ U, int64_t ldu,
-                                  const int* __restrict__ row_ids, int zero_lo, int zero_hi, int S, int npad,
-                                  __nv_bfloat16* __restrict__ out, int* __restrict__ ecol, const int32_t* status) {
-  if (status && *status != GJ_OK) return;
+__device__ __forceinline__ void slice_cols(int warp, int nwarps, int N, int K, const double* __restrict__ U,
+                                           int64_t ldu, const int* __restrict__ row_ids, int zero_lo, int zero_hi,
+                                           int S, int npad, __nv_bfloat16* __restrict__ out,
+                                           int* __restrict__ ecol) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   int rid[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -164,6 +159,25 @@ __global__ void slice_cols_kernel(int N, int K, const double* __restrict__ U, in
     for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
     write_digits(out, S, (int64_t)npad * kKB, (int64_t)j * kKB + lane * 4, x, e);
     if (lane == 0) ecol[j] = e;
+  }
+}
+
+// One launch slices both operands: blocks [0, row_blocks) take the rows of L, the rest the
+// columns of U.
+__global__ void slice_kernel(int row_blocks, int M, int N, int K, const double* __restrict__ L, int64_t ldl,
+                             const int* __restrict__ minus_one_at, const double* __restrict__ U, int64_t ldu,
+                             const int* __restrict__ row_ids, int zero_lo, int zero_hi, int S, int mpad, int npad,
+                             __nv_bfloat16* __restrict__ As, __nv_bfloat16* __restrict__ Bs, int* __restrict__ erow,
+                             int* __restrict__ ecol, const int32_t* status) {
+  if (status && *status != GJ_OK) return;
+  const int wpb = blockDim.x >> 5;
+  if ((int)blockIdx.x < row_blocks) {
+    slice_rows((int)blockIdx.x * wpb + (threadIdx.x >> 5), row_blocks * wpb, M, K, L, ldl, minus_one_at, S, mpad,
+               As, erow);
+  } else {
+    const int b = (int)blockIdx.x - row_blocks;
+    slice_cols(b * wpb + (threadIdx.x >> 5), ((int)gridDim.x - row_blocks) * wpb, N, K, U, ldu, row_ids, zero_lo,
+               zero_hi, S, npad, Bs, ecol);
   }
 }
 
@@ -585,14 +599,13 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   int dev = 0, sms = 0;
   GJ_CUDA(cudaGetDevice(&dev));
   GJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // 8 warps per block, one row (column) per warp per pass
   const int sb = (int)std::min<int64_t>((mpad + 7) / 8, (int64_t)sms * 16);
-  slice_rows_kernel<<<sb, 256, 0, s>>>((int)M, K, L, ldl, l_minus_one_at, S, (int)mpad, As, erow, status);
-  GJ_CUDA(cudaGetLastError());
   const int sc = (int)std::min<int64_t>((npad + 7) / 8, (int64_t)sms * 16);
-  slice_cols_kernel<<<sc, 256, 0, s>>>((int)N, K, U, ldu, u_row_ids, zero_lo, zero_hi, S, (int)npad, Bs, ecol,
-                                       status);
+  slice_kernel<<<sb + sc, 256, 0, s>>>(sb, (int)M, (int)N, K, L, ldl, l_minus_one_at, U, ldu, u_row_ids, zero_lo,
+                                       zero_hi, S, (int)mpad, (int)npad, As, Bs, erow, ecol, status);
   GJ_CUDA(cudaGetLastError());
-  prof_count(2);
+  prof_count(1);
 
   CUtensorMap mapA, mapB;
   gj_status st = make_slice_map(&mapA, As, (int64_t)S * mpad, kTM);
