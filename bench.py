@@ -587,7 +587,8 @@ def run_gpu(args) -> None:
                         "input": "U diag(sigma) V^T, Haar U,V (GPU QR), sigma log-spaced 1..kappa, FP32, seed 1406",
                         "method": "per matrix: reduced-precision blocked GJ (tensor update, x0 slices) + "
                                   "Newton-Schulz, FP64-level residual, ladder 3 -> 5 -> 8 slices",
-                        "launch": f"host worker pool, {args.workers or 8} streams, largest first",
+                        "launch": f"host worker pool, {args.workers or 16} streams, largest first, update grid "
+                                  "capped at 2 x 152 / workers SMs",
                         "x0_slices": args.x0_slices})
         elif args.workload == "inv128":
             cfg.update({"n": W["n"], "input": "N(0,1), seed 1402",
@@ -727,7 +728,7 @@ def main():
     ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
     ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 8)")
     ap.add_argument("--x0-slices", type=int, default=3, help="digit slices of the mixed path's first inverse")
-    ap.add_argument("--workers", type=int, default=8, help="mixedbatch4096: host workers (= streams)")
+    ap.add_argument("--workers", type=int, default=16, help="mixedbatch4096: host workers (= streams)")
     ap.add_argument("--compare-fma", action="store_true", help="mixed workload: also time the FP64-FMA update GJ")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")

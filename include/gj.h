@@ -242,7 +242,7 @@ gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, double* X, int
  *   X          [count] host array of device pointers: FP64 outputs, leading dimension n.
  *              A and X of different matrices must not overlap.
  *   x0_slices, corr_slices, tol, max_iter   as gj_invert_mixed, for every matrix.
- *   workers    host workers (= concurrent streams), 0..64; 0 chooses min(count, 8).
+ *   workers    host workers (= concurrent streams), 0..64; 0 chooses min(count, 16).
  *   status     [count] host out (may be NULL): gj_invert_mixed's status per matrix.
  *   resid, iters, rung, det_sign, det_log2   [count] host outs (may be NULL): per-matrix
  *              values of gj_invert_mixed's outputs.

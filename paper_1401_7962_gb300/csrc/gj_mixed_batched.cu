@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "gj_internal.cuh"
+#include "gj_ozaki.cuh"
 
 extern "C" gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, const int32_t* lda,
                                              const float* const* A, double* const* X, int x0_slices,
@@ -57,8 +58,16 @@ extern "C" gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, co
   std::mutex mu;
   std::string first_error;
 
+  const int nw = (int)std::min<int64_t>(count, workers > 0 ? workers : 16);
+  int sms = 0;
+  GJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // each worker's tensor-core updates take at most twice its share of the SMs, so that a
+  // large update of one matrix does not hold the whole GPU while the other workers' panel
+  // clusters wait for free SMs
+  const int cap = std::max(8, (2 * sms) / nw);
   auto work = [&]() {
     if (cudaSetDevice(dev) != cudaSuccess) return;
+    set_thread_update_cap(cap);
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
@@ -85,8 +94,8 @@ extern "C" gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, co
     }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
+    set_thread_update_cap(0);
   };
-  const int nw = (int)std::min<int64_t>(count, workers > 0 ? workers : 8);
   std::vector<std::thread> pool;
   pool.reserve((size_t)nw);
   for (int w = 0; w < nw; ++w) pool.emplace_back(work);

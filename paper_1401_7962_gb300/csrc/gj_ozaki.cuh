@@ -17,6 +17,11 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S);
 // *status != GJ_OK (status may be null).  max_ctas > 0 caps the persistent grid (one CTA
 // per SM), leaving the other SMs to work on another stream.  prof_name labels the launch for
 // the library's profiling hooks.
+// Default cap of the calling host thread on the persistent grid of ozaki_update when the
+// call passes max_ctas = 0 (0: no cap).  The batched mixed path sets it on its worker
+// threads so that the updates of several matrices share the SMs with their panel clusters.
+void set_thread_update_cap(int ctas);
+
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
                        int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s,

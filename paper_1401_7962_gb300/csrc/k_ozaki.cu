@@ -577,6 +577,12 @@ gj_status make_slice_map(CUtensorMap* map, void* base, int64_t rows, int box_row
 
 }  // namespace
 
+namespace {
+thread_local int t_update_cap = 0;
+}  // namespace
+
+void set_thread_update_cap(int ctas) { t_update_cap = ctas > 0 ? ctas : 0; }
+
 size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S) {
   const int64_t mpad = (M + kTM - 1) / kTM * kTM, npad = (N + kTM - 1) / kTM * kTM;
   return (size_t)S * (mpad + npad) * kKB * 2 + (size_t)(mpad + npad) * sizeof(int) + 256;
@@ -587,6 +593,7 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
                        int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s,
                        int max_ctas, const char* prof_name) {
   if (K < 1 || K > kKB || S < 1 || S > 8) return GJ_ERR_ARG;
+  if (max_ctas <= 0) max_ctas = t_update_cap;
   const int64_t mpad = (M + kTM - 1) / kTM * kTM, npad = (N + kTM - 1) / kTM * kTM;
   uint8_t* p = static_cast<uint8_t*>(ws);
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(p);
