@@ -445,18 +445,29 @@ def run_gpu(args) -> None:
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     prof_ms = ms
+    launches = ctypes.c_int64(0)
     if prof_after:
+        # launch count: one more whole step with the counters on
         L.gj_profile_begin()
-        p0 = time.perf_counter()
         with torch.cuda.stream(stream):
             step()
         torch.cuda.synchronize(dev)
-        prof_ms = 1000.0 * (time.perf_counter() - p0)
-    launches = ctypes.c_int64(0)
-    cnt = L.gj_profile_end(prof_entries, 16, ctypes.byref(launches))
-    if prof_after:
-        extra["profiled_step_ms"] = round(prof_ms, 1)
+        L.gj_profile_end(prof_entries, 16, ctypes.byref(launches))
         launches.value *= args.steps
+        # per-kernel device times: the first 256 matrices on one worker, so that no launch
+        # waits for SMs held by another stream's kernels
+        L.gj_profile_begin()
+        p0 = time.perf_counter()
+        gj.invert_mixed_batched(As[:256], Xs[:256], x0_slices=args.x0_slices, corr_slices=4, tol=1e-12,
+                                max_iter=10, workers=1, stream=stream)
+        torch.cuda.synchronize(dev)
+        prof_ms = 1000.0 * (time.perf_counter() - p0)
+        extra["profile_sample"] = "first 256 matrices, 1 worker, outside the timed steps"
+        extra["profile_sample_ms"] = round(prof_ms, 1)
+        dummy = ctypes.c_int64(0)
+        cnt = L.gj_profile_end(prof_entries, 16, ctypes.byref(dummy))
+    else:
+        cnt = L.gj_profile_end(prof_entries, 16, ctypes.byref(launches))
     ms_max = max_over_ranks(ms, world)
     prof = {}
     for i in range(cnt):
@@ -504,8 +515,7 @@ def run_gpu(args) -> None:
         roof["avg_launch_ms"] = round(avg_ms, 6)
         roof["share_of_step"] = round(d["total_ms"] / prof_ms, 4)
         if args.workload == "mixedbatch4096":
-            roof["note"] = ("launches of all worker streams; they overlap, so share_of_step sums overlapped "
-                            "time and avg_launch_ms includes time shared with other streams' kernels")
+            roof["note"] = "from the 1-worker profile sample (no contention between streams)"
         if dominant == "update_ozaki_wide" and W.get("n", 0) >= 2048:
             cs = min(16, -(-W["n"] // 256))
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -528,16 +538,17 @@ def run_gpu(args) -> None:
         roof["avg_launch_ms"] = round(avg_ms, 6)
         roof["share_of_step"] = round(d["total_ms"] / prof_ms, 4)
         if args.workload == "mixedbatch4096":
-            roof["note"] = ("summed over all worker streams in one profiled step; the streams overlap, so "
-                            "share_of_step counts overlapped time; a panel launch runs on its cluster's "
-                            "4-16 SMs, so its fraction of the whole-GPU FP64 rate is small by construction")
+            roof["note"] = ("from the 1-worker profile sample (no contention between streams); a panel launch "
+                            "runs on its cluster's 1-4 CTAs, so its fraction of the whole-GPU FP64 rate is "
+                            "small by construction")
 
     if args.workload == "mixedbatch4096":
         rung = np.asarray(mixed_state["rung"])
         its = np.asarray(mixed_state["iters"])
         extra["resid_max"] = float(np.max(mixed_state["resid"]))
-        extra["x0_rung_counts"] = {f"{sl}_slices": int((rung == i).sum())
-                                   for i, sl in enumerate([args.x0_slices, max(args.x0_slices, 5), 8])}
+        ladder = np.array([args.x0_slices, max(args.x0_slices, 5), 8])
+        used = ladder[rung]
+        extra["x0_slices_used_counts"] = {f"{sl}_slices": int((used == sl).sum()) for sl in sorted(set(ladder.tolist()))}
         extra["refinement_steps_mean"] = round(float(its.mean()), 3)
     if args.workload == "mixed16384":
         n = W["n"]
@@ -593,8 +604,10 @@ def run_gpu(args) -> None:
         elif args.workload == "mixedbatch4096":
             cfg.update({"count": W["count"], "orders": "U{128..1024}", "kappa": "logU[1e2, 1e8]", "tol": 1e-12,
                         "input": "U diag(sigma) V^T, Haar U,V (GPU QR), sigma log-spaced 1..kappa, FP32, seed 1406",
-                        "method": "per matrix: reduced-precision blocked GJ (tensor update, x0 slices) + "
-                                  "Newton-Schulz, FP64-level residual, ladder 3 -> 5 -> 8 slices",
+                        "method": f"per matrix: blocked GJ with the tensor update at {args.x0_slices} digit slices "
+                                  "(8 = FP64 level) + Newton-Schulz with an FP64-level residual to 1e-12; ladder "
+                                  f"{args.x0_slices} -> {max(args.x0_slices, 5)} -> 8 slices for a matrix that does "
+                                  "not contract",
                         "launch": f"host worker pool, {args.workers or 16} streams, largest first, update grid "
                                   "capped at 2 x 152 / workers SMs",
                         "x0_slices": args.x0_slices})
@@ -735,7 +748,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="inv8192")
     ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
     ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 8)")
-    ap.add_argument("--x0-slices", type=int, default=3, help="digit slices of the mixed path's first inverse")
+    ap.add_argument("--x0-slices", type=int, default=None,
+                    help="digit slices of the mixed path's first inverse (default: 3 for mixed16384, 8 for "
+                         "mixedbatch4096, the fastest measured there)")
     ap.add_argument("--workers", type=int, default=16, help="mixedbatch4096: host workers (= streams)")
     ap.add_argument("--compare-fma", action="store_true", help="mixed workload: also time the FP64-FMA update GJ")
     ap.add_argument("--traffic", type=float, default=None,
@@ -749,6 +764,8 @@ def main():
     ap.add_argument("--n", type=int, default=0,
                     help="order of the single-matrix workload (default: the workload's own); for profiling runs")
     args = ap.parse_args()
+    if args.x0_slices is None:
+        args.x0_slices = 8 if args.workload == "mixedbatch4096" else 3
     if args.warmup < 3 and args.impl == "gj":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -217,7 +217,9 @@ gj_status gj_gemm_update_emulated(int64_t M, int64_t N, int64_t K, const double*
  *   refinement: R = I - A X formed to FP64 level (exact 128-wide chunks of the emulated
  *       update), X <- X + X R with corr_slices slices, until
  *       ||A X - I||_F / (||A||_F ||X||_F) <= tol.  A rung that does not contract is
- *       replaced by the next (x0_slices -> max(x0_slices, 5) -> 8).
+ *       replaced by the next (x0_slices -> max(x0_slices, 5) -> 8); the middle rung is
+ *       skipped when the first ||I - A X0||_F of the failed rung, times 2^-7 per extra
+ *       slice, stays above 1/4.
  *   n, A, lda   FP32 column-major input, device memory, lda >= max(1, n).
  *   X           [n * n] FP64 output, device memory, leading dimension n.
  *   x0_slices, corr_slices   1..8.   tol > 0.   max_iter >= 0 refinement steps per rung.

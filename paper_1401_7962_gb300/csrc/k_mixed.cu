@@ -10,7 +10,9 @@
 // has to be accurate relative to the small R_k -- uses fewer slices.  The iteration stops
 // when ||A X - I||_F / (||A||_F ||X||_F) <= tol.  If the residual does not contract (the
 // first X0 was too inaccurate for this condition number) the next rung of precision is
-// taken: 5 slices for X0, and finally the FP64-level update (8 slices).
+// taken: 5 slices for X0, and finally the FP64-level update (8 slices); the 5-slice rung is
+// skipped when the failed rung's first residual norm shows that 5 slices cannot contract
+// either (each extra slice lowers the truncation by 2^-7).
 #include <math.h>
 
 #include <algorithm>
@@ -195,7 +197,7 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
       if (h.status != GJ_OK) { result = (gj_status)h.status; break; }
       if (det_sign) *det_sign = h.det_sign;
       if (det_log2) *det_log2 = h.det_log2;
-      double prev = INFINITY;
+      double prev = INFINITY, R0 = INFINITY;
       iters = 0;
       for (;;) {
         // R = I - A X (FP64-level: 8 slices, exact 128-wide chunks)
@@ -207,6 +209,7 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
         if ((st = sumsq((int64_t)nn, X, part, dres, nparts, s, &hX2)) != GJ_OK) { result = st; break; }
         r = sqrt(hR2) / (normA * sqrt(hX2));
         if (!(r == r)) r = INFINITY;
+        if (iters == 0 && hR2 == hR2) R0 = sqrt(hR2);
         if (r <= tol) {
           converged = true;
           break;
@@ -223,6 +226,18 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
         ++iters;
       }
       if (result != GJ_OK) break;
+      // next rung: the lowest one whose X0 (truncation 2^-7 smaller per extra slice) would
+      // bring this rung's first ||I - A X0||_F below 1/4, else the FP64-level rung; so a
+      // matrix whose 3-slice X0 is far off goes to 8 slices without a 5-slice X0 between
+      if (!converged && rg < 2) {
+        int nxt = 2;
+        for (int q = rg + 1; q < 2; ++q)
+          if (R0 * ldexp(1.0, -7 * (rungs[q] - rungs[rg])) <= 0.25) {
+            nxt = q;
+            break;
+          }
+        rg = nxt - 1;  // the loop's increment lands on nxt
+      }
     }
     int32_t herr = 0;
     cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

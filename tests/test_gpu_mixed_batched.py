@@ -103,6 +103,33 @@ def test_kappa_1e8_reaches_the_fp64_rung():
     _check_against_oracle(host[0], r["X"][0].cpu().numpy(), {"det_sign": int(r["det_sign"][0])}, 1e-12)
 
 
+def _panel_launches(fn):
+    """Launches of the cluster panel kernel made by fn(), from the library's profiling hooks."""
+    import ctypes
+
+    class Entry(ctypes.Structure):
+        _fields_ = [("kernel", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                    ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+    L = gj.lib()
+    entries = (Entry * 16)()
+    total = ctypes.c_int64(0)
+    L.gj_profile_begin()
+    out = fn()
+    cnt = L.gj_profile_end(entries, 16, ctypes.byref(total))
+    return out, sum(entries[i].launches for i in range(cnt) if entries[i].kernel == b"panel_cluster")
+
+
+def test_ladder_skips_the_middle_rung_when_it_cannot_contract():
+    """kappa = 1e8 from a 3-slice X0: the first residual norm is far above 2^14 / 4, so the
+    5-slice X0 is skipped: two X0 sweeps (3 and 8 slices) of 17 sub-panels of 32 columns
+    each, not three."""
+    host, dev, _ = _batch([520], [1e8], seed=4400)
+    r, panels = _panel_launches(lambda: gj.invert_mixed_batched(dev, x0_slices=3, corr_slices=4, tol=1e-12,
+                                                                 workers=1))
+    assert r["status"] == gj.OK and r["rung"][0] == 2
+    assert panels == 2 * 17, panels
+
+
 def test_nonconvergence_is_per_matrix():
     """tol below what FP64 can reach: every matrix reports GJ_NOT_CONVERGED with its
     residual, and the call returns that status."""
