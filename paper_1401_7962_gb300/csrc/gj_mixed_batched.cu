@@ -20,6 +20,7 @@
 
 #include "gj_internal.cuh"
 #include "gj_ozaki.cuh"
+#include "gj_paths.cuh"
 
 extern "C" gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, const int32_t* lda,
                                              const float* const* A, double* const* X, int x0_slices,
@@ -68,6 +69,7 @@ extern "C" gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, co
   auto work = [&]() {
     if (cudaSetDevice(dev) != cudaSuccess) return;
     set_thread_update_cap(cap);
+    set_thread_panel_rows(128);
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
@@ -95,6 +97,7 @@ extern "C" gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, co
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     set_thread_update_cap(0);
+    set_thread_panel_rows(256);
   };
   std::vector<std::thread> pool;
   pool.reserve((size_t)nw);

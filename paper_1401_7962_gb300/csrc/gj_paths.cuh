@@ -29,6 +29,11 @@ gj_status run_blocked(int64_t n, const double* A, int64_t lda, double* X, int pi
                       int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs = nullptr,
                       int lookahead = 0);
 
+// Rows per CTA that the calling host thread's blocked calls aim at when they size the panel
+// cluster (default 256; at most 16 CTAs per cluster).  The batched mixed path's workers use
+// 128: more CTAs per cluster halve each CTA's FP64 work per pivot step.
+void set_thread_panel_rows(int rows);
+
 // Unblocked Gauss-Jordan over the whole grid, one rank-1 step per launch (any pivoting).
 gj_status run_unblocked(int64_t n, const double* A, int64_t lda, double* X, int pivot_mode, double tau,
                         const CtaOut& out, cudaStream_t s, const Rhs* rhs = nullptr);

@@ -815,10 +815,17 @@ struct WsList {
 
 }  // namespace
 
+namespace {
+thread_local int t_panel_rows = 256;
+}  // namespace
+
+void set_thread_panel_rows(int rows) { t_panel_rows = rows >= 32 ? rows : 256; }
+
 // Choose the cluster size and panel width for order n; returns the shared memory bytes.
 static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* rp_out) {
-  // rp: rows per CTA, whole 32-row blocks dealt round robin
-  int cs = (int)((n + 255) / 256);
+  // rp: rows per CTA, whole 32-row blocks dealt round robin; about t_panel_rows rows per
+  // CTA, at most 16 CTAs
+  int cs = (int)((n + t_panel_rows - 1) / t_panel_rows);
   if (cs < 1) cs = 1;
   if (cs > 16) cs = 16;
   const size_t limit = 220 * 1024;
