@@ -101,7 +101,17 @@ extern "C" gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, co
   };
   std::vector<std::thread> pool;
   pool.reserve((size_t)nw);
-  for (int w = 0; w < nw; ++w) pool.emplace_back(work);
+  for (int w = 0; w < nw; ++w) {
+    try {
+      pool.emplace_back(work);
+    } catch (...) {  // no more threads: the ones started (or this one) take the rest
+      break;
+    }
+  }
+  if (pool.empty()) {
+    work();
+    cudaSetDevice(dev);
+  }
   for (auto& t : pool) t.join();
 
   // the call's status: the first hard error (negative) in matrix order, else the first
