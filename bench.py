@@ -51,7 +51,7 @@ FP64_NOMINAL_GFLOPS = 1250.0
 NCU_TRAFFIC = {
     "update_dfma": None,  # column-window change since profiles/update_dfma_inv6144.md
     # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (96 CTAs)
-    "update_ozaki_wide": {"n": 6144, "bytes": 323.197184e6 + 233.317376e6},
+    "update_ozaki_wide": None,  # the slicing changed since profiles/ozaki_update_kernel_inv6144.md
     "update_ozaki_tc": None,
     # the plan replays one kernel per order bin; traffic summed over those kernels
     "batched_plan": None,
@@ -502,7 +502,7 @@ def run_gpu(args) -> None:
         avg_ms = d["total_ms"] / d["launches"]
         # the profile counts tensor FLOP (S (S + 1) / 2 slice products per FP64 term); the
         # mixed paths run the update with several slice counts, so no single FP64 equivalent
-        S = None if args.workload in ("mixed16384", "mixedbatch4096") else (args.slices or 8)
+        S = None if args.workload in ("mixed16384", "mixedbatch4096") else (args.slices or 7)
         pairs = S * (S + 1) // 2 if S else None
         tc_fl = d["flops"] / d["launches"]
         t = NCU_TRAFFIC.get(dominant)
@@ -546,7 +546,7 @@ def run_gpu(args) -> None:
         rung = np.asarray(mixed_state["rung"])
         its = np.asarray(mixed_state["iters"])
         extra["resid_max"] = float(np.max(mixed_state["resid"]))
-        ladder = np.array([args.x0_slices, max(args.x0_slices, 5), 8])
+        ladder = np.array([min(args.x0_slices, 7), min(max(args.x0_slices, 5), 7), 7])
         used = ladder[rung]
         extra["x0_slices_used_counts"] = {f"{sl}_slices": int((used == sl).sum()) for sl in sorted(set(ladder.tolist()))}
         extra["refinement_steps_mean"] = round(float(its.mean()), 3)
@@ -554,7 +554,7 @@ def run_gpu(args) -> None:
         n = W["n"]
         extra["resid"] = mixed_state.get("resid")
         extra["refinement_steps"] = mixed_state.get("iters")
-        extra["x0_rung_slices"] = [args.x0_slices, max(args.x0_slices, 5), 8][mixed_state.get("rung", 0)]
+        extra["x0_rung_slices"] = [min(args.x0_slices, 7), min(max(args.x0_slices, 5), 7), 7][mixed_state.get("rung", 0)]
         # the plain FP64-level Gauss-Jordan on the same matrix (converted exactly to FP64)
         dA64 = dA32.double().t().contiguous().t()
         for eng, label in ((gj.UPDATE_TC_OZAKI, "fp64_gj_tensor_update"), (gj.UPDATE_DFMA, "fp64_gj_fma_update")):
@@ -593,7 +593,8 @@ def run_gpu(args) -> None:
                "profile": prof}
         if args.workload == "inv8192":
             eng = "fp64 fma" if (args.update == "dfma") else \
-                f"tensor cores: bf16 digit slices (S={args.slices or 8}), exact fp32 group sums, int64 recombination"
+                f"tensor cores: bf16 balanced 8-bit digit slices (S={args.slices or 7}), exact fp32 group sums, " \
+                "int64 recombination"
             cfg.update({"n": W["n"], "update": args.update, "update_engine": eng,
                         "input": "N(0,1) + 0.1 n I, seed 1403"})
         elif args.workload == "mixed16384":
@@ -605,8 +606,8 @@ def run_gpu(args) -> None:
             cfg.update({"count": W["count"], "orders": "U{128..1024}", "kappa": "logU[1e2, 1e8]", "tol": 1e-12,
                         "input": "U diag(sigma) V^T, Haar U,V (GPU QR), sigma log-spaced 1..kappa, FP32, seed 1406",
                         "method": f"per matrix: blocked GJ with the tensor update at {args.x0_slices} digit slices "
-                                  "(8 = FP64 level) + Newton-Schulz with an FP64-level residual to 1e-12; ladder "
-                                  f"{args.x0_slices} -> {max(args.x0_slices, 5)} -> 8 slices for a matrix that does "
+                                  "(7 = FP64 level) + Newton-Schulz with an FP64-level residual to 1e-12; ladder "
+                                  f"{args.x0_slices} -> {max(args.x0_slices, 5)} -> 7 slices for a matrix that does "
                                   "not contract",
                         "launch": f"host worker pool, {args.workers or 16} streams, largest first, update grid "
                                   "capped at 2 x 152 / workers SMs",
@@ -747,9 +748,9 @@ def main():
     ap.add_argument("--impl", choices=["gj", "reference"], default="gj")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="inv8192")
     ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
-    ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 8)")
+    ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 7)")
     ap.add_argument("--x0-slices", type=int, default=None,
-                    help="digit slices of the mixed path's first inverse (default: 3 for mixed16384, 8 for "
+                    help="digit slices of the mixed path's first inverse (default: 3 for mixed16384, 7 for "
                          "mixedbatch4096, the fastest measured there)")
     ap.add_argument("--workers", type=int, default=16, help="mixedbatch4096: host workers (= streams)")
     ap.add_argument("--compare-fma", action="store_true", help="mixed workload: also time the FP64-FMA update GJ")
@@ -765,7 +766,7 @@ def main():
                     help="order of the single-matrix workload (default: the workload's own); for profiling runs")
     args = ap.parse_args()
     if args.x0_slices is None:
-        args.x0_slices = 8 if args.workload == "mixedbatch4096" else 3
+        args.x0_slices = 7 if args.workload == "mixedbatch4096" else 3
     if args.warmup < 3 and args.impl == "gj":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -76,8 +76,8 @@ typedef struct gj_opts {
                             n >= 512), 1 = FP64 FMA, 2 = FP64 emulated on BF16 tcgen05 tensor
                             cores (digit-split operands, exact FP32 partial sums, FP64
                             recombination; 128-column panels) */
-  int32_t slices;        /* digit slices per operand for update 2: 1..8, 0 = 8 (truncation
-                            below 2^-56 of each row / column scale) */
+  int32_t slices;        /* digit slices per operand for update 2: 1..8, 0 = 7 (8 bits per
+                            slice; 7 slices round below 2^-56 of each row / column scale) */
   int32_t* piv_rows;     /* optional out [n], host or device: row position interchanged
                             with position k at step k */
   int32_t* piv_cols;     /* optional out [n], host or device: same for columns */
@@ -144,7 +144,11 @@ gj_status gj_solve_ex(const gj_opts* opts, int64_t n, int64_t nrhs, const double
 
 /*
  * gj_invert_batched -- invert `count` independent matrices of uneven orders in one
- * persistent launch (one CTA per matrix; work items taken largest order first).
+ * persistent launch (one CTA per matrix; work items taken largest order first).  Each
+ * matrix gets the method of Section 2 as gj_invert does: [A | I] reduced to [I | A^-1]
+ * (eqs. 1-12) by pivot-row scaling (eq. 14) and elimination (eq. 15), pivots of largest
+ * magnitude (obs. 2-3) with the interchanges undone at the end (obs. 3), det A as the
+ * signed product of the pivots (eq. 13).  Batching itself is not in the paper.
  *   count      number of matrices, >= 0.
  *   nmax       host: upper bound of the orders (sizes the launch); 0 means 128.  Must
  *              be <= 128 (GJ_ERR_UNSUPPORTED otherwise).
@@ -167,21 +171,24 @@ gj_status gj_invert_batched(int64_t count, int32_t nmax, const int32_t* n, const
 
 /*
  * gj_invert_batched_noalloc -- gj_invert_batched without any device allocation.
- * The paper has no counterpart: this entry point exists for callers that cannot
- * allocate device memory when they invert (code running while a stream capture is
- * active in global mode, where cudaMalloc is illegal; real-time loops that must not
- * take the allocator's locks or risk its latency or failure; programs that hand all
- * device memory to their own pool).  Arguments, results and stream ordering are those
- * of gj_invert_batched.
+ * The paper has no counterpart.  Some callers cannot allocate device memory at the point
+ * where they invert: real-time loops that must not take the allocator's locks or risk its
+ * latency or an out-of-memory failure in the middle of a frame; programs that handed all
+ * device memory to their own pool at start-up, so that a library allocation fails or
+ * fragments it; code that by its own rules allocates only during initialisation.  This
+ * entry point serves them.  Arguments, results and stream ordering are those of
+ * gj_invert_batched.
  *   - Scratch (work order, histogram, queue counter) lives in a static device array of
  *     GJ_NOALLOC_MAX_COUNT + 131 int32 (about 4 MiB) that every GPU loading the library
  *     holds until the process exits.  count > GJ_NOALLOC_MAX_COUNT returns
  *     GJ_ERR_UNSUPPORTED before any launch (gj_last_error() says why).
- *   - The first call on a device looks up the array's device address (once per
- *     device, with that device current); make that first call before any stream
- *     capture.
- *   - Every call shares the one array: calls whose execution overlaps on the GPU race
- *     and must be serialised by the caller.  Each call clears what must start at zero.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current) and keeps it for later calls; the lookup is repeated when the device's
+ *     context has changed since (after cudaDeviceReset, for instance).  Make that first
+ *     call before any stream capture.
+ *   - Every call shares the one array, which keeps the last call's contents: each call
+ *     clears what must start at zero, and calls whose execution overlaps on the GPU (other
+ *     streams, other host threads) race on it and must be serialised by the caller.
  *   - Calls no cudaMalloc, cudaFree or allocating library routine.
  */
 #define GJ_NOALLOC_MAX_COUNT 1048576
@@ -197,8 +204,8 @@ gj_status gj_invert_batched_noalloc(int64_t count, int32_t nmax, const int32_t* 
  *   L          [ldl * K] device, column-major M x K, ldl >= M.
  *   U          [ldu * N] device, column-major K x N, ldu >= K.
  *   C          [ldc * N] device, column-major M x N, ldc >= M; updated in place.
- *   slices     digits per operand entry, 1..8 (7 bits each; 7 or 8 reach FP64-level error:
- *              truncation below 2^-7*slices relative to each row / column scale).
+ *   slices     balanced base-256 digits per operand entry, 1..8 (8 bits each; 7 or 8 reach
+ *              FP64-level error: below 2^-8*slices relative to each row / column scale).
  *   stream     cudaStream_t (NULL = legacy default stream).
  * Synchronous (waits for the stream: it reports device-side wait expiry as
  * GJ_ERR_TIMEOUT).  Uses a stream-ordered workspace of about
@@ -260,7 +267,9 @@ gj_status gj_invert_mixed_batched(int64_t count, const int32_t* n, const int32_t
                                   int8_t* det_sign, double* det_log2, void* stream);
 
 /* A batched plan fixes the orders (host copy given at creation), precomputes the
- * largest-first work order and launch shape, and can be replayed as a CUDA graph. */
+ * largest-first work order and launch shape, and can be replayed as a CUDA graph.  Every
+ * matrix of a planned batch is inverted by the method of Section 2 (eqs. 1-15, obs. 2-3,
+ * det by eq. 13), as in gj_invert_batched; the plan only schedules that work. */
 typedef struct gj_plan gj_plan;
 
 /*
@@ -312,8 +321,9 @@ int32_t gj_batched_plan_bins(const gj_plan* plan, int32_t* lo, int32_t* hi, int6
                              float* tuned_us, int32_t max_bins);
 
 /*
- * gj_batched_plan_execute -- run a planned batch on `stream`.  Argument meaning as in
- * gj_invert_batched (device arrays).  With use_graph != 0 the launch sequence is
+ * gj_batched_plan_execute -- run a planned batch on `stream`: every matrix is inverted by
+ * eqs. 1-15 with the pivoting of obs. 2-3 and its determinant formed by eq. 13, as in
+ * gj_invert_batched.  Argument meaning as in gj_invert_batched (device arrays).  With use_graph != 0 the launch sequence is
  * captured once into a CUDA graph for these pointer arrays and replayed afterwards
  * (re-captured if the pointers or stream change).
  */
@@ -348,6 +358,18 @@ int gj_profile_end(gj_profile_entry* out, int max_entries, int64_t* launches);
  * paper has no counterpart.  Call it with no library work in flight.
  */
 gj_status gj_trim_memory(void);
+
+/*
+ * gj_set_wait_limit_ns -- limit, in nanoseconds, of the pipeline waits of the tensor-core
+ * update kernel (gj_gemm_update_emulated, and the update of the blocked path and of
+ * gj_invert_mixed); 0 restores the default of 2 s.  The paper has no counterpart: the limit
+ * exists so that a test can make such a wait expire and check what follows.  On expiry
+ * the kernel stops issuing work, waits (with the full 2 s limit) for the tile loads and
+ * MMAs it already issued, frees its tensor memory and exits; the call returns
+ * GJ_ERR_TIMEOUT.  Process-wide, read at every launch; set it with no library work in
+ * flight.  The waits of the cluster kernels keep their fixed 2 s limit.
+ */
+gj_status gj_set_wait_limit_ns(uint64_t ns);
 
 /* gj_status_string -- static text for a status code. */
 const char* gj_status_string(int status);

@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
     L.gj_version.argtypes = []
     L.gj_trim_memory.restype = I
     L.gj_trim_memory.argtypes = []
+    L.gj_set_wait_limit_ns.restype = I
+    L.gj_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
     _LIB = L
     return L
 
@@ -100,6 +102,11 @@ def status_string(status: int) -> str:
 
 def last_error() -> str:
     return lib().gj_last_error().decode()
+
+
+def set_wait_limit_ns(ns: int) -> None:
+    """``gj_set_wait_limit_ns``: limit of the tensor-core update's pipeline waits (0 = 2 s)."""
+    lib().gj_set_wait_limit_ns(int(ns))
 
 
 # ----------------------------------------------------------------- marshalling helpers

@@ -24,7 +24,7 @@ void set_thread_update_cap(int ctas);
 
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
-                       int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s,
+                       int64_t ldc, int S, void* ws, int32_t* err, int32_t* status, cudaStream_t s,
                        int max_ctas = 0, const char* prof_name = "update_ozaki_tc");
 
 }  // namespace gj

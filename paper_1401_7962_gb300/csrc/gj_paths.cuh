@@ -21,7 +21,7 @@ struct Rhs {
 // Blocked Gauss-Jordan (partial or no pivoting): panels of width b eliminated by one
 // thread-block cluster, then a rank-b update of all other columns.  A (ld lda) -> X (ld n).
 // update: 0 = automatic (tensor-core update from kTensorUpdateMinN), 1 = FP64 FMA, 2 = tensor
-// cores with `slices` digit slices (0 = 8).
+// cores with `slices` digit slices (0 = 7, the FP64 level).
 constexpr int kTensorUpdateMinN = 512;
 // lookahead: 0 = automatic (on for the tensor-core update from kLookaheadMinN), 1 = off, 2 = on.
 constexpr int kLookaheadMinN = 2048;

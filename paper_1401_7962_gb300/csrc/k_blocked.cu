@@ -859,7 +859,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   // 128 / b cluster sub-panels with FP64 updates inside the panel; the FP64 update path
   // uses the cluster panel width directly.
   const bool tc = (update == 2) || (update == 0 && n >= kTensorUpdateMinN);
-  const int S = slices > 0 ? slices : 8;
+  const int S = slices > 0 ? slices : 7;  // 7 balanced 8-bit digits: FP64 level
   const int Bw = tc ? 128 : b;
   // look-ahead: the next outer panel is reduced on a second stream while the update of the
   // other columns runs (tensor-core path with at least two outer panels)

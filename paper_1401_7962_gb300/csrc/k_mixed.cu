@@ -1,18 +1,19 @@
 // k_mixed.cu -- reduced-precision Gauss-Jordan followed by Newton-Schulz refinement.
 //
 // X0 comes from the blocked Gauss-Jordan of eqs. 14-15 whose rank-128 updates run on the
-// BF16 tensor cores with only S digit slices (S = 1: about 8 bits, S = 2: 15, S = 3: 22
-// bits of each row / column scale) while pivot search, division and the determinant stay
-// in FP64.  Accuracy is then recovered by Newton-Schulz refinement
+// BF16 tensor cores with only S digit slices (8 bits each: S = 1 about BF16's 8-bit
+// significand, S = 2 a split-BF16 pair of 16 bits, S = 3 24 bits, FP32's significand, of
+// each row / column scale) while pivot search, division and the determinant stay in FP64.
+// Accuracy is then recovered by Newton-Schulz refinement
 //     R_k = I - A X_k,   X_{k+1} = X_k + X_k R_k,   so   I - A X_{k+1} = R_k^2,
 // with R_k formed to FP64 level: the K = n product A X_k is summed in exact 128-wide
-// chunks of the tensor-core update (8 slices), and the correction X_k R_k -- which only
+// chunks of the tensor-core update (7 slices), and the correction X_k R_k -- which only
 // has to be accurate relative to the small R_k -- uses fewer slices.  The iteration stops
 // when ||A X - I||_F / (||A||_F ||X||_F) <= tol.  If the residual does not contract (the
 // first X0 was too inaccurate for this condition number) the next rung of precision is
-// taken: 5 slices for X0, and finally the FP64-level update (8 slices); the 5-slice rung is
+// taken: 5 slices for X0, and finally the FP64-level update (7 slices); the 5-slice rung is
 // skipped when the failed rung's first residual norm shows that 5 slices cannot contract
-// either (each extra slice lowers the truncation by 2^-7).
+// either (each extra slice lowers the truncation by 2^-8).
 #include <math.h>
 
 #include <algorithm>
@@ -22,6 +23,8 @@
 
 namespace gj {
 namespace {
+
+constexpr int kFp64Slices = 7;  // digit slices of the FP64-level update
 
 __global__ void f32_to_f64_kernel(int64_t n, const float* __restrict__ A, int64_t lda, double* __restrict__ D,
                                   double* __restrict__ negD) {
@@ -169,10 +172,10 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
     if ((result = sumsq((int64_t)nn, Ad, part, dres, nparts, s, &hA2)) != GJ_OK) break;
     const double normA = sqrt(hA2);
 
-    // precision ladder for X0: requested slices, then 5, then the FP64-level 8.  The update
-    // truncation is below (S + 2) 128 2^-7S of the scales per panel; Newton-Schulz needs
-    // roughly that times kappa below 1: 5 slices (~2.6e-8) serve kappa up to ~1e6-1e7.
-    int rungs[3] = {x0_slices, std::max(x0_slices, 5), 8};
+    // precision ladder for X0: requested slices, then 5, then the FP64-level 7.  The update
+    // error is below (S + 2) 128 2^-8S of the scales per panel; Newton-Schulz needs roughly
+    // that times kappa below 1: 5 slices (~1e-9) serve kappa up to ~1e8.
+    int rungs[3] = {std::min(x0_slices, kFp64Slices), std::min(std::max(x0_slices, 5), kFp64Slices), kFp64Slices};
     double r = INFINITY;
     int iters = 0, rung_used = 0;
     bool converged = false;
@@ -200,10 +203,10 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
       double prev = INFINITY, R0 = INFINITY;
       iters = 0;
       for (;;) {
-        // R = I - A X (FP64-level: 8 slices, exact 128-wide chunks)
+        // R = I - A X (FP64-level: 7 slices, exact 128-wide chunks)
         identity_kernel<<<sms * 8, 256, 0, s>>>(n, R);
         prof_count(1);
-        if ((st = product_chunks(n, negA, X, R, 8, ws, err, s)) != GJ_OK) { result = st; break; }
+        if ((st = product_chunks(n, negA, X, R, kFp64Slices, ws, err, s)) != GJ_OK) { result = st; break; }
         double hR2 = 0.0, hX2 = 0.0;
         if ((st = sumsq((int64_t)nn, R, part, dres, nparts, s, &hR2)) != GJ_OK) { result = st; break; }
         if ((st = sumsq((int64_t)nn, X, part, dres, nparts, s, &hX2)) != GJ_OK) { result = st; break; }
@@ -226,13 +229,13 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
         ++iters;
       }
       if (result != GJ_OK) break;
-      // next rung: the lowest one whose X0 (truncation 2^-7 smaller per extra slice) would
-      // bring this rung's first ||I - A X0||_F below 1/4, else the FP64-level rung; so a
-      // matrix whose 3-slice X0 is far off goes to 8 slices without a 5-slice X0 between
+      // next rung: the lowest one whose X0 (error 2^-8 smaller per extra slice) would bring
+      // this rung's first ||I - A X0||_F below 1/4, else the FP64-level rung; so a matrix
+      // whose 3-slice X0 is far off goes to 7 slices without a 5-slice X0 between
       if (!converged && rg < 2) {
         int nxt = 2;
         for (int q = rg + 1; q < 2; ++q)
-          if (R0 * ldexp(1.0, -7 * (rungs[q] - rungs[rg])) <= 0.25) {
+          if (R0 * ldexp(1.0, -8 * (rungs[q] - rungs[rg])) <= 0.25) {
             nxt = q;
             break;
           }

@@ -2,22 +2,27 @@
 //
 // gj_invert_batched takes its scratch (the largest-first work order, the order-size
 // histogram and the queue counter) from the stream-ordered allocator.  Some callers
-// cannot allocate at the point where they invert: code running while a stream capture
-// is active in global mode (cudaMalloc is illegal there), real-time loops that must
-// not take the allocator's locks or risk its latency or failure, and programs that hand
-// all device memory to their own pool.  This variant keeps that scratch in a
-// file-scope device array instead: it is loaded with the library and every GPU that
-// loads the library holds it (about 4 MiB) until the process exits.
+// cannot allocate at the point where they invert: real-time loops that must not take the
+// allocator's locks or risk its latency or failure, programs that handed all device
+// memory to their own pool, code that allocates only during initialisation.  This
+// variant keeps that scratch in a file-scope device array instead: it is loaded with the
+// library and every GPU that loads the library holds it (about 4 MiB) until the process
+// exits.
 //
 // The array's name is a host-side stand-in in host code, not a device address, so the
 // host asks the runtime for the address (cudaGetSymbolAddress) once per device, with
 // that device current, and passes the result to the kernels.  The first call on a
-// device does this set-up; make that first call before any stream capture.
+// device does this set-up; make that first call before any stream capture.  The address
+// is kept together with the identifier of the context it was looked up in, and looked up
+// again when the device's current context is another one (a cudaDeviceReset destroys the
+// context the address belonged to).
 //
 // All calls share the one array, and it keeps the last call's contents: the histogram
 // and the queue counter are cleared by every call before use.  Calls whose execution
 // overlaps on the GPU (different streams, or concurrent host threads) race on the
 // array and must be serialised by the caller.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "gj_internal.cuh"
@@ -33,18 +38,49 @@ static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 int32_t* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once per device).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identifier of the calling thread's current context, 0 when none is current or the driver
+// does not offer context identifiers (the address is then looked up on every call).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device, looked up once per device and
+// context.
 gj_status scratch_address(int32_t** out) {
   int dev = 0;
   GJ_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return GJ_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
     g_addr[dev] = static_cast<int32_t*>(p);
+    g_ctx[dev] = current_context_id();  // the lookup makes the device's primary context current
   }
   *out = g_addr[dev];
   return GJ_OK;

@@ -4,22 +4,24 @@
 // width).  GB300's FP64 units deliver about 1.2 TFLOP/s, its BF16 tensor cores about
 // 1.9 PFLOP/s, so the update is emulated (an error-free splitting in the manner of the
 // Ozaki scheme):
-//   * every row i of L is scaled by a power of two 2^e_i with max_k |L_ik| < 2^e_i and
-//     every column j of U by 2^f_j; the scaled entries, in (-1, 1), are cut into S signed
-//     7-bit digits (magnitude 0..127, exactly representable in BF16):
-//         L_ik = 2^e_i sum_s a_s[i,k] 2^-7(s+1)   (truncated after S digits)
+//   * every row i of L gets the power of two 2^e_i with max_k |L_ik| < 2^e_i, and every
+//     column j of U a 2^f_j.  The scaled entry L_ik 2^-(e_i+1), in (-1/2, 1/2), is rounded
+//     to 8S - 1 fractional bits and written in balanced base 256: S signed digits
+//     a_s in [-128, 128] (exactly representable in BF16) with
+//         L_ik ~ 2^(e_i+1) sum_s a_s[i,k] 2^-8(s+1),   error <= 2^(e_i - 8S);
 //   * the digit products with s + t <= S - 1 are accumulated by the tensor cores in FP32
-//     in tensor memory, one accumulator per group g = s + t.  Each digit product is
-//     < 2^14, each pair's sum over k <= 128 terms < 2^21 and each group (<= 8 pairs)
-//     < 2^24, so every FP32 partial sum is an exact integer;
-//   * the epilogue combines the groups exactly in a 64-bit integer (weights 2^-7(g+2)),
-//     converts once to FP64, scales by 2^(e_i + f_j) and adds to C with one FP64 FMA.
-// The truncation error per entry is below 2^-7S relative to the row / column scale (S = 7:
-// 2^-49; S = 8: 2^-56), i.e. at the level of an FP64 product's rounding.
+//     in tensor memory, one accumulator per group g = s + t.  Each digit product is at
+//     most 2^14, each pair's sum over k <= 128 terms at most 2^21 and each group (<= 8
+//     pairs) at most 2^24, so every FP32 partial sum is an exact integer;
+//   * the epilogue combines the groups exactly in a 64-bit integer (weights 2^(41 - 8g)),
+//     converts once to FP64, scales by 2^(e_i + f_j - 55) and adds to C.
+// The error per entry is below (S + 2) K 2^(e_i + f_j - 8S) plus the FP64 roundings (S = 7:
+// 2^-56 of the scales, the level of an FP64 product's rounding, with 28 digit products per
+// term; 7-bit truncated digits needed 8 slices and 36 products for the same level).
 //
 // Kernel shape: persistent, one CTA per SM walking 128 x 64 tiles of C.  Warp 0 issues the
 // TMA loads (all S digit slices of the U tile stay resident; the L slices stream through a
-// 4-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), eight
+// 2-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), eight
 // warps run the epilogue (TMEM lane = row of the tile).  Every mbarrier wait is bounded in
 // time; on expiry the kernel records an error, drains its own TMA loads and MMAs, frees its
 // tensor memory and returns.
@@ -30,6 +32,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "gj_internal.cuh"
@@ -55,7 +58,7 @@ constexpr int kEpiSlices = kEpiWarps / 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr int kEpiCols = kTN / kEpiSlices;  // columns per epilogue thread
 constexpr int kCSm = kEpiCols / 2; // of those, prefetched into shared memory (the rest load in the final pass)
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: default pipeline wait, and every teardown drain
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTM, kTN);
 
 // ---------------------------------------------------------------- digit slicing
@@ -67,36 +70,43 @@ __device__ __forceinline__ int exp_of(double x) {
   return E == 0 ? -100000 : E - 1022;
 }
 
-// floor(|x| * 2^(7S - e)) for |x| < 2^e (subnormals flush to 0)
-__device__ __forceinline__ unsigned long long digits_of(double x, int e, int S) {
+// round(|x| 2^(8S - 1 - e)) for |x| < 2^e (at most 2^(8S - 1); subnormals flush to 0)
+__device__ __forceinline__ unsigned long long magnitude_of(double x, int e, int S) {
   const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
   const int E = static_cast<int>((b >> 52) & 0x7FF);
   if (E == 0) return 0ull;
   const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int shift = (E - 1023) - 52 + 7 * S - e;
-  if (shift >= 0) return M << shift;
+  const int shift = (E - 1023) - 52 + 8 * S - 1 - e;
+  if (shift >= 0) return M << shift;  // shift <= 8S - 54, so M << shift < 2^(8S - 1)
   if (shift <= -64) return 0ull;
-  return M >> (-shift);
+  return (M + (1ull << (-shift - 1))) >> (-shift);  // round half up
 }
 
+// The S balanced base-256 digits of four entries (digit 0 the most significant), written to
+// slices s = 0..S-1 at out + s * slice_stride + off.
 __device__ __forceinline__ void write_digits(__nv_bfloat16* out, int S, int64_t slice_stride, int64_t off,
                                              const double (&x)[4], int e) {
-  unsigned long long m[4];
-  int neg[4];
+  long long v[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    m[q] = digits_of(x[q], e, S);
-    neg[q] = x[q] < 0.0;
+    const long long m = static_cast<long long>(magnitude_of(x[q], e, S));
+    v[q] = x[q] < 0.0 ? -m : m;
   }
-  for (int s = 0; s < S; ++s) {
-    const int sh = 7 * (S - 1 - s);
-    __align__(8) __nv_bfloat16 v[4];
+  for (int s = S - 1; s >= 0; --s) {
+    __align__(8) __nv_bfloat16 d[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int d = static_cast<int>((m[q] >> sh) & 0x7Full);
-      v[q] = __float2bfloat16_rn(static_cast<float>(neg[q] ? -d : d));
+      int r;
+      if (s > 0) {
+        r = static_cast<int>(v[q] & 255);  // low 8 bits (two's complement)
+        if (r > 128) r -= 256;             // balanced: r in [-127, 128]
+        v[q] = (v[q] - r) >> 8;            // exact
+      } else {
+        r = static_cast<int>(v[q]);        // |r| <= 128 (see the header)
+      }
+      d[q] = __float2bfloat16_rn(static_cast<float>(r));
     }
-    *reinterpret_cast<uint2*>(out + s * slice_stride + off) = *reinterpret_cast<const uint2*>(v);
+    *reinterpret_cast<uint2*>(out + s * slice_stride + off) = *reinterpret_cast<const uint2*>(d);
   }
 }
 
@@ -244,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     ozaki_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                         int N, int mpad, int npad, int S, int nkc, int tiles_m, int tiles_n, int ts_lo, int ts_hi,
                         int skip_lo, int skip_hi, double* __restrict__ C, int64_t ldc, const int* __restrict__ erow,
-                        const int* __restrict__ ecol, int32_t* err, const int32_t* status) {
+                        const int* __restrict__ ecol, int32_t* err, int32_t* status, uint64_t wait_ns) {
   if (status && *status != GJ_OK) return;
   const int tiles_n_act = tiles_n - (ts_hi - ts_lo);
   const int ntiles = tiles_m * tiles_n_act;
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (new_column(idx)) {
           // the MMAs of the previous tile column must have finished reading the resident U
           // slices (bar_bempty completes one phase per tile column that is followed by another)
-          if (b_issued > 0 && !tc::mbar_wait_backoff(&bar_bempty, (uint32_t)((b_issued - 1) & 1), kWaitNs)) {
+          if (b_issued > 0 && !tc::mbar_wait_backoff(&bar_bempty, (uint32_t)((b_issued - 1) & 1), wait_ns)) {
             atomicExch(err, 10);
             s_abort = 1;
             break;
@@ -331,9 +341,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (S >= kStages) {
               const int g = (sl >= kStages) ? sl - kStages : S - kStages + sl;
               const int tl = (sl >= kStages) ? local : local - 1;
-              free_ok = tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(tl & 1), kWaitNs);
+              free_ok = tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(tl & 1), wait_ns);
             } else {
-              free_ok = tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), kWaitNs);
+              free_ok = tc::mbar_wait_backoff(&bar_empty[stage], (uint32_t)((use - 1) & 1), wait_ns);
             }
           }
           if (!free_ok) {
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int idx = t_begin; idx < t_end && !s_abort; ++idx, ++local) {
         bool ok = true;
         if (new_column(idx)) {
-          ok = tc::mbar_wait(&bar_bfull, (uint32_t)(b_used & 1), kWaitNs);
+          ok = tc::mbar_wait(&bar_bfull, (uint32_t)(b_used & 1), wait_ns);
           ++b_used;
           if (!ok) {
             atomicExch(err, 20);
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int sl = 0; sl < S && ok; ++sl, ++it) {
           const int stage = it % kStages, use = it / kStages;
-          if (!tc::mbar_wait(&bar_full[stage], (uint32_t)(use & 1), kWaitNs)) {
+          if (!tc::mbar_wait(&bar_full[stage], (uint32_t)(use & 1), wait_ns)) {
             ok = false;
             break;
           }
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t target = (uint32_t)(kEpiWarps * (local + 1));
         const uint64_t w0 = tc::global_timer_ns();
         while (tc::counter_load_acquire(&s_drained) < target) {
-          if (s_abort || tc::global_timer_ns() - w0 > kWaitNs) {
+          if (s_abort || tc::global_timer_ns() - w0 > wait_ns) {
             ok = false;
             break;
           }
@@ -450,13 +460,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // is polled without sleeping
         int ok0 = 0;
         if (lane == 0)
-          ok0 = ((g == S - 1) ? tc::mbar_wait(&bar_gready[g], (uint32_t)(local & 1), kWaitNs)
-                              : tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(local & 1), kWaitNs)) &&
+          ok0 = ((g == S - 1) ? tc::mbar_wait(&bar_gready[g], (uint32_t)(local & 1), wait_ns)
+                              : tc::mbar_wait_backoff(&bar_gready[g], (uint32_t)(local & 1), wait_ns)) &&
                 !s_abort;
         ok = __shfl_sync(0xffffffffu, ok0, 0) != 0;  // warp-uniform
         if (!ok) break;
         tc::tc_fence_after();
-        const int sh = 55 - 7 * (g + 2);
+        const int sh = 57 - 8 * (g + 2);  // group weight 2^-8(g+2) of 2^(e_i+1+f_j+1), over 2^(e_i+f_j-55)
         // 16 columns at a time (keeps the live registers within one CTA per SM)
 #pragma unroll
         for (int half = 0; half < kEpiCols / 16; ++half) {
@@ -518,17 +528,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   // ---------------- teardown: drain own async work (bounded), then free tensor memory
+  // After an abort the drains below wait with the full default limit whatever limit the
+  // pipeline waits had: every TMA load this CTA issued lands in its own shared memory and
+  // every MMA it issued writes its own tensor memory, so both must have completed before
+  // the CTA frees that memory and exits.  A drain that still expires records its own code
+  // (40: a U-slice load, 41: an L-slice load, 42: the MMAs); the CTA then exits with that
+  // copy or MMA still outstanding, which only a broken device could cause.
   __syncthreads();
   if (s_abort) {
     if (warp == 0 && lane == 0) {
-      if (b_issued > 0) tc::mbar_wait(&bar_bfull, (uint32_t)((b_issued - 1) & 1), kWaitNs);
+      if (b_issued > 0 && !tc::mbar_wait(&bar_bfull, (uint32_t)((b_issued - 1) & 1), kWaitNs)) atomicExch(err, 40);
       for (int st = 0; st < kStages; ++st)
-        if (issued_uses[st] > 0) tc::mbar_wait(&bar_full[st], (uint32_t)((issued_uses[st] - 1) & 1), kWaitNs);
+        if (issued_uses[st] > 0 && !tc::mbar_wait(&bar_full[st], (uint32_t)((issued_uses[st] - 1) & 1), kWaitNs))
+          atomicExch(err, 41);
     }
     if (warp == 1 && lane == 0) {
       tc::mma_commit(&bar_fin);
-      tc::mbar_wait(&bar_fin, 0, kWaitNs);
+      if (!tc::mbar_wait(&bar_fin, 0, kWaitNs)) atomicExch(err, 42);
     }
+    // the caller's status (when it passes one) fails at once, so that the kernels queued
+    // after this one skip their work instead of running on a partly updated array
+    if (tid == 0 && status) atomicCAS(status, (int32_t)GJ_OK, (int32_t)GJ_ERR_TIMEOUT);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -579,6 +599,9 @@ gj_status make_slice_map(CUtensorMap* map, void* base, int64_t rows, int box_row
 
 namespace {
 thread_local int t_update_cap = 0;
+// Limit of the update kernel's pipeline waits in nanoseconds (0 = the 2 s default); set by
+// gj_set_wait_limit_ns to exercise the expiry path.
+std::atomic<uint64_t> g_wait_ns{0};
 }  // namespace
 
 void set_thread_update_cap(int ctas) { t_update_cap = ctas > 0 ? ctas : 0; }
@@ -590,7 +613,7 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S) {
 
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
-                       int64_t ldc, int S, void* ws, int32_t* err, const int32_t* status, cudaStream_t s,
+                       int64_t ldc, int S, void* ws, int32_t* err, int32_t* status, cudaStream_t s,
                        int max_ctas, const char* prof_name) {
   if (K < 1 || K > kKB || S < 1 || S > 8) return GJ_ERR_ARG;
   if (max_ctas <= 0) max_ctas = t_update_cap;
@@ -634,13 +657,15 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   const int ntiles = tiles_m * (tiles_n - (ts_hi - ts_lo));
   if (ntiles <= 0) return GJ_OK;
   const int grid = std::min(ntiles, (max_ctas > 0 && max_ctas < sms) ? max_ctas : sms);
+  const uint64_t lim = g_wait_ns.load(std::memory_order_relaxed);
+  const uint64_t wait_ns = lim ? lim : kWaitNs;
   {
     // tensor FLOP: S (S + 1) / 2 digit-slice products per FP64 product term
     ProfScope ps(s, prof_name, 0.5 * S * (S + 1) * 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
                  16.0 * (double)M * (double)N);
     ozaki_update_kernel<<<grid, kThreads, smem, s>>>(mapA, mapB, (int)M, (int)N, (int)mpad, (int)npad, S, nkc,
                                                     tiles_m, tiles_n, ts_lo, ts_hi, zero_lo, zero_hi, C, ldc, erow,
-                                                    ecol, err, status);
+                                                    ecol, err, status, wait_ns);
   }
   GJ_CUDA(cudaGetLastError());
   prof_count(1);
@@ -683,4 +708,9 @@ extern "C" gj_status gj_gemm_update_emulated(int64_t M, int64_t N, int64_t K, co
     st = GJ_ERR_TIMEOUT;
   }
   return st;
+}
+
+extern "C" gj_status gj_set_wait_limit_ns(uint64_t ns) {
+  gj::g_wait_ns.store(ns, std::memory_order_relaxed);
+  return GJ_OK;
 }

@@ -3,10 +3,14 @@ FP64 oracle, on A = U diag(sigma) V^T with Haar U, V and log-spaced sigma, store
 
 What is checked: the normalised residual ||A X - I||_F / (||A||_F ||X||_F) reaches the
 requested tolerance (1e-12); the refined X agrees with the oracle's inverse of the same
-FP32 matrix (converted exactly to FP64) to the forward-error level of a backward-stable
-inverse, 64 n kappa eps relative in the Frobenius norm; the determinant sign equals the
-oracle's and log2|det| (from the reduced-precision pivots) is within the error that the
-X0 precision allows, n kappa 2^-(7 S) relative."""
+FP32 matrix (converted exactly to FP64) element by element, to the forward-error level of a
+backward-stable inverse (64 n kappa_1 eps max|X|, the tolerance of the FP64 paths), and in
+the Frobenius norm; the determinant sign equals the oracle's.  log2|det| comes from the
+pivots of the last X0 sweep, whose updates carry an error of about 2^-8S of the scales:
+it must match the oracle to n kappa 2^-(8 S) relative (at least 1e-12, the FP64 paths'
+tolerance, which the 7-slice rung meets for small kappa), capped at 1/4 so that the
+assertion can always fail.  One case (n = 2304) is large enough for the look-ahead
+schedule of the blocked sweep (n >= 2048)."""
 import math
 
 import numpy as np
@@ -29,7 +33,8 @@ def built():
     gj.lib()
 
 
-@pytest.mark.parametrize("n,kappa,x0", [(300, 1e2, 1), (520, 1e4, 2), (700, 1e6, 5), (1000, 1e6, 3)])
+@pytest.mark.parametrize("n,kappa,x0", [(300, 1e2, 1), (520, 1e4, 2), (700, 1e6, 5), (1000, 1e6, 3),
+                                        (640, 1e6, 7), (400, 1e2, 7), (2304, 1e6, 3)])
 def test_mixed_refined_inverse(n, kappa, x0):
     A32 = wl.svd_conditioned(n, kappa, seed=5000 + n, dtype=np.float32)
     A = A32.astype(np.float64)
@@ -45,13 +50,18 @@ def test_mixed_refined_inverse(n, kappa, x0):
     kap = np.linalg.cond(A, 2)
     rel = np.linalg.norm(X - o["X"]) / np.linalg.norm(o["X"])
     assert rel <= 64 * n * kap * EPS, (rel, kap)
+    kap1 = np.linalg.cond(A, 1)
+    diff = np.max(np.abs(X - o["X"]))
+    assert diff <= 64 * n * kap1 * EPS * np.max(np.abs(o["X"])), (diff, kap1)
     assert r["det_sign"] == o["det_sign"]
-    S_used = [x0, max(x0, 5), 8][r["rung"]]
-    assert abs(r["det_log2"] - o["det_log2"]) <= max(1e-9, n * kap * 2.0 ** (-7 * S_used)) * max(1.0, abs(o["det_log2"]))
+    S_used = [min(x0, 7), min(max(x0, 5), 7), 7][r["rung"]]
+    rel_tol = min(0.25, max(1e-12, n * kap * 2.0 ** (-8 * S_used)))
+    assert abs(r["det_log2"] - o["det_log2"]) <= rel_tol * max(1.0, abs(o["det_log2"])), \
+        (r["det_log2"], o["det_log2"], S_used)
 
 
 def test_mixed_ladder_climbs_when_x0_too_coarse():
-    """kappa = 1e6 with 1-slice X0 cannot contract (2^-7 kappa >> 1): the ladder moves up."""
+    """kappa = 1e6 with 1-slice X0 cannot contract (2^-8 kappa >> 1): the ladder moves up."""
     n = 400
     A32 = wl.svd_conditioned(n, 1e6, seed=77, dtype=np.float32)
     r = gj.invert_mixed(torch.from_numpy(np.asfortranarray(A32)).cuda(), x0_slices=1, tol=1e-12)

@@ -1,12 +1,15 @@
 """The emulated FP64 rank-k update (gj_gemm_update_emulated: BF16 tcgen05 tensor cores,
 exact digit splitting) against an FP64 product computed on the host.
 
-Error bound (derived from the splitting): every entry of L is cut to S 7-bit digits of
-its row scale 2^e_i (error < 2^(e_i - 7S)), every entry of U likewise with its column
-scale 2^f_j (2 K 2^(e_i + f_j - 7S) over the k sum), the digit pairs with s + t >= S are
-dropped (fewer than S - 1 pairs of weight 2^-7(S+2) and size < 2^14 per term: < (S - 1) K
-2^(e_i + f_j - 7S)), and the kept products are summed exactly; the entry (i, j) of L U is
-therefore off by less than (S + 2) K 2^(e_i + f_j - 7S), plus the FP64 roundings of the
+Error bound (derived from the splitting): every entry of L is rounded to 8S - 1 fractional
+bits of its row scale 2^(e_i + 1) and written as S balanced base-256 digits in [-128, 128]
+(error <= 2^(e_i - 8S)), every entry of U likewise with its column scale (together
+<= 2 K 2^(e_i + f_j - 8S) over the k sum, to first order); the digit pairs with s + t >= S
+are dropped (at most S - 1 pairs per group, digit products <= 2^14, weights
+2^-8(s+t+2) of 2^(e_i + f_j + 2): < 1.01 (S - 1) K 2^(e_i + f_j - 8S)); the kept products are
+summed exactly, and the integer combination drops the bits of the two lowest groups below
+2^(e_i + f_j - 55) (< 2 2^(e_i + f_j - 55)).  The entry (i, j) of L U is therefore off by
+less than (S + 2) K 2^(e_i + f_j - 8S) + 2^(e_i + f_j - 54), plus the FP64 roundings of the
 int64 -> FP64 conversion and the final add (<= 4 K eps sum_k |L_ik||U_kj| + 2 eps |C_new|).
 The test checks exactly that bound.
 """
@@ -52,8 +55,8 @@ def run(M, N, K, S, rng, ldl_pad=0, scale_rows=False):
     ref = C + L @ U
     e = scale_exp(L, 1)[:, None]
     f = scale_exp(U, 0)[None, :]
-    bound = (S + 2.0) * K * np.exp2((e + f - 7 * S).astype(np.float64)) + 2 * EPS * np.abs(ref) + \
-        4 * K * EPS * (np.abs(L) @ np.abs(U))
+    bound = (S + 2.0) * K * np.exp2((e + f - 8 * S).astype(np.float64)) + np.exp2((e + f - 54).astype(np.float64)) + \
+        2 * EPS * np.abs(ref) + 4 * K * EPS * (np.abs(L) @ np.abs(U))
     return got, ref, bound
 
 

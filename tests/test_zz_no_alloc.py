@@ -1,13 +1,12 @@
 """gj_invert_batched_noalloc, the batched entry point that allocates no device memory.
 
-It serves callers that cannot allocate when they invert: code running while a stream
-capture is active in global mode (where cudaMalloc is illegal), real-time loops that must
-not take the allocator's locks or risk its latency or failure, and programs that hand all
-device memory to their own pool.  Its scratch lives in a static device array shared by
-every call, so the test makes two calls in a row on two different batches (different
-counts, orders and contents) and checks each against the allocating entry point,
-gj_invert_batched, on the same input: scratch left over from the first call would show
-up in the second.  Both calls go through the C ABI.
+It serves callers that cannot allocate when they invert: real-time loops that must not take
+the allocator's locks or risk its latency or an out-of-memory failure, programs that handed
+all device memory to their own pool, and code that allocates only during initialisation.
+Its scratch lives in a static device array shared by every call, so the test makes two calls
+in a row on two different batches (different counts, orders and contents) and checks each
+against the allocating entry point, gj_invert_batched, on the same input: scratch left over
+from the first call would show up in the second.  Both calls go through the C ABI.
 
 This file is named to be collected last; it passes alone in a fresh process (the first
 call on the device does the array's set-up) and after the other tests.
