@@ -199,17 +199,21 @@ def measured_peaks() -> dict:
         return {}
 
 
-def roofline_tensor(tensor_tflops: float, fp64_equiv_tflops: float, pairs: int, traffic) -> dict:
+def roofline_tensor(tensor_tflops: float, fp64_equiv_tflops, pairs, traffic) -> dict:
+    """Roofline entry of a tensor-core update kernel.  With a single slice count, `achieved`
+    is the method's own work (2 M N K FP64 FLOP per launch) per second; the BF16 digit-slice
+    products the tensor cores actually run (pairs per FP64 term) are reported beside it."""
     peaks = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", 1720.6))
     src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"
-    return {"bound": "tensor", "achieved": round(tensor_tflops, 2), "peak": peak, "unit": "TFLOP/s",
-            "frac": round(tensor_tflops / peak, 4), "traffic": traffic,
+    ach = fp64_equiv_tflops if fp64_equiv_tflops is not None else tensor_tflops
+    return {"bound": "tensor", "achieved": round(ach, 3), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(ach / peak, 5), "traffic": traffic,
             "peak_source": f"BF16 dense sustained {src} (kernel timed inside a long step)",
-            "work": (f"{pairs} BF16 digit-slice products per FP64 product term (2 K FLOP each per element)" if pairs
-                     else "BF16 digit-slice products, S (S + 1) / 2 per FP64 product term, S per call (X0, residual, "
-                          "correction slices)"),
-            "fp64_equivalent_tflops": round(fp64_equiv_tflops, 3) if fp64_equiv_tflops is not None else None}
+            "work": (f"method FLOP (2 M N K per launch, FP64 accurate); the tensor cores run {pairs} BF16 "
+                     "digit-slice products per FP64 term" if pairs else
+                     "BF16 digit-slice FLOP (S (S + 1) / 2 products per FP64 term; the mixed path runs several S)"),
+            "tensor_slice_tflops": round(tensor_tflops, 2), "tensor_slice_frac": round(tensor_tflops / peak, 4)}
 
 
 def roofline_fp64(achieved_gflops: float, traffic) -> dict:
@@ -302,7 +306,13 @@ def metric_name(workload: str) -> str:
 
 # ----------------------------------------------------------------- GPU arm
 
+# The other workloads measured beside the 8192 inversion in the default run (one GPU):
+# (workload, timed steps, first-inverse slices of the mixed paths).
+SUB_WORKLOADS = (("inv128", 50, None), ("batch200k", 10, None), ("mixed16384", 2, 3), ("mixedbatch4096", 2, 7))
+
+
 def run_gpu(args) -> None:
+    import copy
     import torch
     world, rank, local = dist_env()
     if world > 1:
@@ -314,8 +324,43 @@ def run_gpu(args) -> None:
     from paper_1401_7962_gb300 import _build
     _build.build()
     import paper_1401_7962_gb300 as gj
-    import ctypes
     L = gj.lib()
+    line = measure(args, gj, L, dev, world, rank)
+    if rank == 0 and world == 1 and args.workload == "inv8192" and not args.n and not args.headline_only:
+        subs = {}
+        for wk, steps, x0 in SUB_WORKLOADS:
+            a2 = copy.copy(args)
+            a2.workload, a2.steps, a2.slices, a2.update, a2.count = wk, steps, 0, "auto", 0
+            if x0 is not None:
+                a2.x0_slices = x0
+            sub = measure(a2, gj, L, dev, world, rank)
+            subs[sub["config"]["workload"]] = sub_entry(sub)
+            torch.cuda.synchronize(dev)
+            torch.cuda.empty_cache()
+            L.gj_trim_memory()
+        line["config"]["configs"] = subs
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def sub_entry(sub: dict) -> dict:
+    """The measurement of one more workload, as an entry of the headline line's config."""
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "roofline", "cpu_baseline", "e2e", "clocks",
+            "gpu_launches")
+    e = {k: sub.get(k) for k in keep}
+    cfg = dict(sub["config"])
+    cfg.pop("profile", None)
+    e["config"] = cfg
+    return e
+
+
+def measure(args, gj, L, dev, world: int, rank: int) -> dict:
+    """Time one workload (warm-up, then args.steps steps) and return its JSON line (a dict)."""
+    import ctypes
+    import torch
     W = dict(WORKLOADS[args.workload])
     if args.count and "count" in W:
         W["count"] = args.count
@@ -412,6 +457,8 @@ def run_gpu(args) -> None:
                 raise RuntimeError(f"gj_invert_ex failed: {gj.status_string(stc)} {gj.last_error()}")
 
         opts.slices = args.slices
+        opts.panel = args.panel
+        opts.update_sms = args.update_sms
         dominant = "update_dfma" if args.workload == "inv8192" else "cluster_single"
         h2d = d2h = n * n * 8
 
@@ -550,6 +597,8 @@ def run_gpu(args) -> None:
         used = ladder[rung]
         extra["x0_slices_used_counts"] = {f"{sl}_slices": int((used == sl).sum()) for sl in sorted(set(ladder.tolist()))}
         extra["refinement_steps_mean"] = round(float(its.mean()), 3)
+    if args.workload == "mixedbatch4096":
+        extra.update(batched_fp64_arm(gj, As, Xs, sizes, flops_step, mixed_state, args.workers, dev))
     if args.workload == "mixed16384":
         n = W["n"]
         extra["resid"] = mixed_state.get("resid")
@@ -624,10 +673,73 @@ def run_gpu(args) -> None:
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches.value)}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        return line
+    return {}
+
+
+def batched_fp64_arm(gj, As, Xs, sizes, flops, mixed_state, workers: int, dev) -> dict:
+    """Plain FP64 Gauss-Jordan of the same FP32 matrices (converted exactly to FP64) through the
+    public single-matrix call, one host worker thread and stream per worker as in the mixed
+    path, timed on the wall clock; then, outside the timing, the per-matrix error of both
+    arms against the oracle on the smallest matrices and their residuals on a sample."""
+    import threading
+    import torch
+    import oracle
+    order = np.argsort(-sizes, kind="stable")
+    workers = max(1, workers or 16)
+    Ys = [torch.empty_like(x) for x in Xs]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(workers)]
+    nxt = [0]
+    lock = threading.Lock()
+    errs = []
+
+    def work(w):
+        st = streams[w]
+        while True:
+            with lock:
+                q = nxt[0]
+                nxt[0] += 1
+            if q >= len(order):
+                return
+            m = int(order[q])
+            with torch.cuda.stream(st):
+                A64 = As[m].to(torch.float64)
+                r = gj.invert(A64, gj.PIVOT_PARTIAL, out=Ys[m], stream=st)
+            if r["status"] != 0:
+                errs.append((m, r["status"]))
+
+    def run_all():
+        nxt[0] = 0
+        ts = [threading.Thread(target=work, args=(w,)) for w in range(workers)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        torch.cuda.synchronize(dev)
+
+    run_all()  # warm-up
+    t0 = time.perf_counter()
+    run_all()
+    dt = time.perf_counter() - t0
+    out = {"fp64_gj_batched": {"gflops": flops / dt / 1e9, "matrices_per_s": len(As) / dt, "s_per_batch": dt,
+                               "method": "FP64-level blocked GJ (tensor-core update, 7 slices) of every matrix "
+                                         f"through gj_invert_ex, {workers} host workers with one stream each",
+                               "failures": len(errs)}}
+    # per-matrix error against the oracle (smallest matrices) and residuals (sample)
+    sample = [int(m) for m in np.argsort(sizes, kind="stable")[:4]]
+    e_mixed, e_plain, r_plain = [], [], []
+    for m in sample:
+        A = As[m].double().cpu().numpy()
+        o = oracle.invert(A, oracle.PIVOT_PARTIAL)
+        nx = np.linalg.norm(o["X"])
+        e_mixed.append(float(np.linalg.norm(Xs[m].cpu().numpy() - o["X"]) / nx))
+        Y = Ys[m].cpu().numpy()
+        e_plain.append(float(np.linalg.norm(Y - o["X"]) / nx))
+        r_plain.append(float(np.linalg.norm(A @ Y - np.eye(A.shape[0])) / (np.linalg.norm(A) * np.linalg.norm(Y))))
+    out["oracle_sample"] = {"matrices": sample, "orders": [int(sizes[m]) for m in sample],
+                            "mixed_rel_err_F": e_mixed, "fp64_gj_rel_err_F": e_plain,
+                            "fp64_gj_resid": r_plain}
+    return out
 
 
 def _profile_struct():
@@ -749,6 +861,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="inv8192")
     ap.add_argument("--update", choices=["auto", "dfma", "ozaki"], default="auto")
     ap.add_argument("--slices", type=int, default=0, help="digit slices of the tensor-core update (0 = 7)")
+    ap.add_argument("--panel", type=int, default=0, help="cluster panel width of the blocked path (0 = library choice)")
+    ap.add_argument("--update-sms", type=int, default=0,
+                    help="SMs of the wide update under look-ahead (0 = library choice)")
     ap.add_argument("--x0-slices", type=int, default=None,
                     help="digit slices of the mixed path's first inverse (default: 3 for mixed16384, 7 for "
                          "mixedbatch4096, the fastest measured there)")
@@ -764,6 +879,9 @@ def main():
                     help="matrices in the batched workload (default: the workload's own); for profiling runs")
     ap.add_argument("--n", type=int, default=0,
                     help="order of the single-matrix workload (default: the workload's own); for profiling runs")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="measure only the selected workload (the default 8192 run also measures the other "
+                         "workloads and reports them under config.configs)")
     args = ap.parse_args()
     if args.x0_slices is None:
         args.x0_slices = 7 if args.workload == "mixedbatch4096" else 3

@@ -88,6 +88,8 @@ typedef struct gj_opts {
                             n >= 2048), 1 = off, 2 = on.  On: the next 128-column panel is
                             reduced on a second stream while the rank-128 update of the
                             other columns runs (same arithmetic, same results) */
+  int32_t update_sms;    /* look-ahead: SMs of the persistent grid of the wide rank-128 update;
+                            the panel stream keeps the others.  0 = library choice */
 } gj_opts;
 
 /*
@@ -218,27 +220,55 @@ gj_status gj_gemm_update_emulated(int64_t M, int64_t N, int64_t K, const double*
  * gj_invert_mixed -- inverse of an FP32 matrix by reduced-precision Gauss-Jordan plus
  * Newton-Schulz refinement (not in the paper; an accelerated variant of eqs. 14-15).
  *   X0: blocked Gauss-Jordan (partial pivoting) whose rank-128 updates run on the BF16
- *       tensor cores with x0_slices 7-bit digit slices per operand (1: ~8 bits, 2: ~15,
- *       3: ~22 bits of each row / column scale); pivot search, division and log2|det|
- *       stay FP64.
+ *       tensor cores with x0_slices balanced 8-bit digit slices per operand (1: 8 bits,
+ *       2: 16, 3: 24 bits of each row / column scale; 7: FP64 level); pivot search,
+ *       division and log2|det| stay FP64.
  *   refinement: R = I - A X formed to FP64 level (exact 128-wide chunks of the emulated
  *       update), X <- X + X R with corr_slices slices, until
  *       ||A X - I||_F / (||A||_F ||X||_F) <= tol.  A rung that does not contract is
- *       replaced by the next (x0_slices -> max(x0_slices, 5) -> 8); the middle rung is
- *       skipped when the first ||I - A X0||_F of the failed rung, times 2^-7 per extra
- *       slice, stays above 1/4.
+ *       replaced by the next (x0_slices -> max(x0_slices, 5) -> 7, each capped at 7); the
+ *       middle rung is skipped when the first ||I - A X0||_F of the failed rung, times
+ *       2^-8 per extra slice, stays above 1/4.
  *   n, A, lda   FP32 column-major input, device memory, lda >= max(1, n).
  *   X           [n * n] FP64 output, device memory, leading dimension n.
  *   x0_slices, corr_slices   1..8.   tol > 0.   max_iter >= 0 refinement steps per rung.
  *   resid_out, iters_out, rung_out   host outputs (may be NULL): final normalised residual,
  *               refinement steps of the last rung, index of that rung (0..2).
- *   det_sign, det_log2   host outputs (may be NULL): from the pivots of the last X0.
+ *   det_sign, det_log2   host outputs (may be NULL): from the pivots of the last X0 (eq. 13),
+ *               so as accurate as that X0: relative error of log2|det| about
+ *               n kappa 2^-8S for S slices (FP64 level at S = 7 for a well-conditioned A).
  * Returns GJ_NOT_CONVERGED when no rung reaches tol (X holds the last iterate).
  * Synchronous.  Workspace: about 4 n^2 doubles plus the blocked path's.
  */
 gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, double* X, int x0_slices, int corr_slices,
                           double tol, int max_iter, double* resid_out, int* iters_out, int* rung_out, int* det_sign,
                           double* det_log2, void* stream);
+
+/* Arithmetic of the reduced-precision first inverse of the mixed path (gj_invert_mixed_prec).
+ * The update's operands are cut into S balanced 8-bit digits of each row / column scale and
+ * the digit products with s + t <= S - 1 are summed exactly on the BF16 tensor cores, so S
+ * sets how many significant bits of each operand take part: */
+typedef enum gj_prec {
+  GJ_PREC_FP64 = 0,          /* S = 7: 56 bits, the FP64-level update (no reduced precision) */
+  GJ_PREC_BF16 = 1,          /* S = 1: 8 bits, BF16's significand; one product per term */
+  GJ_PREC_FP16 = 2,          /* S = 2: 16 bits, covering FP16's 11-bit significand */
+  GJ_PREC_SPLIT_BF16_3 = 3,  /* S = 2: a hi + lo pair of 8-bit digits and the three products
+                                hi*hi + hi*lo + lo*hi (the split-BF16 3-term scheme) */
+  GJ_PREC_TF32x3 = 4         /* S = 3: 24 bits, FP32's significand, as three TF32 products reach */
+} gj_prec;
+/* The digits are fixed point relative to the largest entry of their row (column), not
+ * floating point per entry: an entry far below its row's largest keeps fewer significant
+ * bits than BF16 / FP16 / TF32 rounding would leave it, with the same normwise error. */
+
+/*
+ * gj_invert_mixed_prec -- gj_invert_mixed with the first inverse's arithmetic named by a
+ * gj_prec value (and correction products of 4 slices, 32 bits).  Not in the paper.
+ * Arguments, outputs, ladder and status as for gj_invert_mixed; GJ_ERR_ARG for an unknown
+ * prec.  GJ_PREC_FP64 inverts at the FP64 level first, so refinement only polishes.
+ */
+gj_status gj_invert_mixed_prec(int64_t n, const float* A, int64_t lda, double* X, int prec, double tol, int max_iter,
+                               double* resid_out, int* iters_out, int* rung_out, int* det_sign, double* det_log2,
+                               void* stream);
 
 /*
  * gj_invert_mixed_batched -- gj_invert_mixed over a batch of FP32 matrices of different

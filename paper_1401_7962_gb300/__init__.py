@@ -26,6 +26,8 @@ PATH_AUTO, PATH_CTA, PATH_BLOCKED, PATH_UNBLOCKED, PATH_CLUSTER = 0, 1, 2, 3, 4
 BATCHED_WARP4, BATCHED_WARP8, BATCHED_CTA64, BATCHED_CTA128, BATCHED_CTA256, BATCHED_CTA512 = range(6)
 BATCHED_NAMES = ["warp4", "warp8", "cta64", "cta128", "cta256", "cta512"]
 UPDATE_AUTO, UPDATE_DFMA, UPDATE_TC_OZAKI = 0, 1, 2
+PREC_FP64, PREC_BF16, PREC_FP16, PREC_SPLIT_BF16_3, PREC_TF32x3 = 0, 1, 2, 3, 4
+PREC_SLICES = {PREC_FP64: 7, PREC_BF16: 1, PREC_FP16: 2, PREC_SPLIT_BF16_3: 2, PREC_TF32x3: 3}
 
 
 class GJError(RuntimeError):
@@ -38,7 +40,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("tau", ctypes.c_double), ("panel", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("update", ctypes.c_int32), ("slices", ctypes.c_int32),
                 ("piv_rows", ctypes.c_void_p), ("piv_cols", ctypes.c_void_p), ("pivots", ctypes.c_void_p),
-                ("fail_step", ctypes.c_void_p), ("lookahead", ctypes.c_int32)]
+                ("fail_step", ctypes.c_void_p), ("lookahead", ctypes.c_int32), ("update_sms", ctypes.c_int32)]
 
 
 _LIB = None
@@ -70,6 +72,8 @@ def lib() -> ctypes.CDLL:
     L.gj_gemm_update_emulated.argtypes = [I64, I64, I64, P, I64, P, I64, P, I64, I, P]
     L.gj_invert_mixed.restype = I
     L.gj_invert_mixed.argtypes = [I64, P, I64, P, I, I, D, I, P, P, P, P, P, P]
+    L.gj_invert_mixed_prec.restype = I
+    L.gj_invert_mixed_prec.argtypes = [I64, P, I64, P, I, D, I, P, P, P, P, P, P]
     L.gj_invert_mixed_batched.restype = I
     L.gj_invert_mixed_batched.argtypes = [I64, P, P, P, P, I, I, D, I, I, P, P, P, P, P, P, P]
     L.gj_batched_plan_create.restype = I
@@ -170,7 +174,7 @@ def _stream_handle(stream) -> int:
 
 def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, path: int = PATH_AUTO,
            panel: int = 0, update: int = UPDATE_AUTO, slices: int = 0, stream=None, record: bool = False,
-           lookahead: int = 0):
+           lookahead: int = 0, update_sms: int = 0):
     """Invert one square matrix with ``gj_invert_ex``.
 
     ``A`` and ``out`` may live on the host or on the device (the library stages host
@@ -195,6 +199,7 @@ def invert(A, pivot_mode: int = PIVOT_PARTIAL, out=None, *, tau: float = 0.0, pa
     o.update = int(update)
     o.slices = int(slices)
     o.lookahead = int(lookahead)
+    o.update_sms = int(update_sms)
     rec = {}
     fs = ctypes.c_int64(-1)
     if record:
@@ -314,6 +319,29 @@ def invert_mixed(A32, out=None, *, x0_slices: int = 3, corr_slices: int = 4, tol
                            ctypes.addressof(sg), ctypes.addressof(lg), _stream_handle(stream))
     if st < 0:
         raise GJError(st, "gj_invert_mixed")
+    return {"X": out, "status": st, "resid": r.value, "iters": it.value, "rung": rg.value, "det_sign": sg.value,
+            "det_log2": lg.value}
+
+
+def invert_mixed_prec(A32, prec: int, out=None, *, tol: float = 1e-12, max_iter: int = 10, stream=None) -> dict:
+    """``gj_invert_mixed_prec``: as ``invert_mixed`` with the first inverse's arithmetic named by
+    a ``PREC_*`` value.  Returns the same dict."""
+    L = lib()
+    if A32.ndim != 2 or A32.shape[0] != A32.shape[1] or str(A32.dtype) != "torch.float32":
+        raise ValueError("square float32 torch tensor expected")
+    n = int(A32.shape[0])
+    s0, s1 = A32.stride()
+    if n > 1 and (s0 != 1 or s1 < n):
+        raise ValueError("matrix must be column-major")
+    import torch
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float64, device=A32.device).t().contiguous().t()
+    r, it, rg, sg, lg = ctypes.c_double(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+    st = L.gj_invert_mixed_prec(n, _ptr(A32), max(1, int(s1) if n > 1 else 1), _ptr(out), int(prec), float(tol),
+                                int(max_iter), ctypes.addressof(r), ctypes.addressof(it), ctypes.addressof(rg),
+                                ctypes.addressof(sg), ctypes.addressof(lg), _stream_handle(stream))
+    if st < 0:
+        raise GJError(st, "gj_invert_mixed_prec")
     return {"X": out, "status": st, "resid": r.value, "iters": it.value, "rung": rg.value, "det_sign": sg.value,
             "det_log2": lg.value}
 

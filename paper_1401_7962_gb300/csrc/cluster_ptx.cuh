@@ -17,6 +17,12 @@ __device__ __forceinline__ uint32_t map_rank(uint32_t local, int rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
   return r;
 }
+// 32-bit load from (possibly another CTA's) shared memory at a shared::cluster address.
+__device__ __forceinline__ int ld_cluster_s32(uint32_t raddr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(raddr) : "memory");
+  return v;
+}
 // 16-byte store into another CTA's shared memory, counted in bytes on that CTA's mbarrier.
 __device__ __forceinline__ void st_async16(uint32_t raddr, int4 v, uint32_t rbar) {
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"

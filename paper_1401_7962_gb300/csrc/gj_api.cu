@@ -163,7 +163,7 @@ static gj_status run_single_device(const gj_opts& o, int64_t n, const double* dA
     case 2:
       if (pivot_mode == GJ_PIVOT_FULL) return GJ_ERR_UNSUPPORTED;
       return run_blocked(n, dA, lda, dX, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s, nullptr,
-                         o.lookahead);
+                         o.lookahead, o.update_sms);
     case 3:
       return run_unblocked(n, dA, lda, dX, pivot_mode, o.tau, out, s);
     case 4:
@@ -222,7 +222,7 @@ gj_status gj_invert_ex(const gj_opts* opts, int64_t n, const double* A, int64_t 
   if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
   if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
   if (o.path < 0 || o.path > 4 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8) return GJ_ERR_ARG;
-  if (o.lookahead < 0 || o.lookahead > 2) return GJ_ERR_ARG;
+  if (o.lookahead < 0 || o.lookahead > 2 || o.update_sms < 0) return GJ_ERR_ARG;
   if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
   if (n == 0) {
     if (det_sign) *det_sign = 1;
@@ -313,7 +313,7 @@ gj_status gj_solve_ex(const gj_opts* opts, int64_t n, int64_t nrhs, const double
   if (pivot_mode < GJ_PIVOT_NONE || pivot_mode > GJ_PIVOT_FULL) return GJ_ERR_ARG;
   if (!(o.tau >= 0.0)) return GJ_ERR_ARG;
   if (o.path < 0 || o.path > 3 || o.path == 1 || o.update < 0 || o.update > 2 || o.slices < 0 || o.slices > 8 ||
-      o.lookahead < 0 || o.lookahead > 2)
+      o.lookahead < 0 || o.lookahead > 2 || o.update_sms < 0)
     return GJ_ERR_ARG;
   if (o.panel != 0 && o.panel != 16 && o.panel != 32 && o.panel != 64 && o.panel != 128) return GJ_ERR_ARG;
   if (n == 0) {
@@ -393,7 +393,7 @@ gj_status gj_solve_ex(const gj_opts* opts, int64_t n, int64_t nrhs, const double
     rhs.ldx = dldx;
     if (path == 2)
       GJ_TRY(run_blocked(n, dA, dlda, nullptr, pivot_mode, o.tau, o.panel, o.update, o.slices, out, s, &rhs,
-                         o.lookahead));
+                         o.lookahead, o.update_sms));
     else
       GJ_TRY(run_unblocked(n, dA, dlda, nullptr, pivot_mode, o.tau, out, s, &rhs));
 

@@ -24,10 +24,11 @@ struct Rhs {
 // cores with `slices` digit slices (0 = 7, the FP64 level).
 constexpr int kTensorUpdateMinN = 512;
 // lookahead: 0 = automatic (on for the tensor-core update from kLookaheadMinN), 1 = off, 2 = on.
+// update_sms: SMs of the wide update's grid under look-ahead (0 = automatic).
 constexpr int kLookaheadMinN = 2048;
 gj_status run_blocked(int64_t n, const double* A, int64_t lda, double* X, int pivot_mode, double tau, int panel,
                       int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs = nullptr,
-                      int lookahead = 0);
+                      int lookahead = 0, int update_sms = 0);
 
 // Rows per CTA that the calling host thread's blocked calls aim at when they size the panel
 // cluster (default 256; at most 16 CTAs per cluster).  The batched mixed path's workers use

@@ -56,7 +56,7 @@ struct PanelSmem {
   static size_t bytes(int cs, int rp, int bb) {
     size_t s = sizeof(PanelCand) * (size_t)(kSlots * cs + 1);
     s += sizeof(double) * (size_t)(rp + 1) * bb;  // Wp, leading dimension rp + 1
-    s += sizeof(double) * (size_t)rp;             // lrow
+    s += sizeof(double) * (size_t)rp * 2;         // lrow (two steps)
     s += sizeof(int) * (size_t)rp * 2;            // posl, act
     return (s + 15) & ~size_t(15);
   }
@@ -96,12 +96,62 @@ __device__ __forceinline__ void warp_argmax3(uint64_t& v, int& key, int& il) {
 // -N M^-1 (N their panel values at the start, M^-1 the panel's pivot block at the end) and
 // get that from fixup_used_rows_kernel on the whole GPU afterwards.
 //
-// Step t: every CTA waits on its own mbarrier for the candidates of all CTAs, takes the
-// same winner, updates column t+1 of its active rows (eq. 15), finds its candidate for step
-// t+1 and stores it with its eq. 14 row into every CTA's shared memory (st.async, counted
-// on the receiver's mbarrier of that slot), then applies eq. 15 to the other columns.
-// There is no cluster-wide barrier per step: three slots guarantee that a slot is only
-// rewritten after every CTA has finished the step that read it.  Waits are bounded.
+// Each CTA splits its warps in two groups.  The critical warps (C, warps 0-3) carry the
+// chain that decides the pivots: step t waits on the CTA's own mbarrier for the candidates
+// of all CTAs, takes the same winner everywhere, applies the eq. 15 update of steps t - 1
+// and t to column t + 1 of the active rows, finds the CTA's candidate for step t + 1 and
+// stores it with its eq. 14 row into every CTA's shared memory (st.async, counted on the
+// receiver's mbarrier of that slot).  The bulk warps (B, warps 4-15) apply eq. 14 / eq. 15
+// of step s to the other columns one step behind, while C runs the exchange of the next
+// step: step s skips column s + 1 (C already applied steps s - 1 and s to it) and column
+// s + 2 (C applies steps s and s + 1 to it in step s + 1).  Two shared-memory step counters
+// (release / acquire) order the groups: B starts step s once C has finished column s + 1 of
+// step s; C builds the record of its step-(t + 1) candidate only once B has finished step
+// t - 1 (the record applies step t to the candidate row on the fly).  There is no
+// cluster-wide barrier per step: three slots guarantee that a slot is only rewritten after
+// every CTA has finished the step that read it (B included: a CTA pushes its step-(t + 1)
+// candidate only after its B has finished step t - 1).  Every wait is bounded.
+__device__ __forceinline__ void group_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// barrier over `count` threads of named barrier `id`, returns whether any of them passed pred != 0
+__device__ __forceinline__ int group_any(int id, int count, int pred) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(pred), "r"(id), "r"(count)
+      : "memory");
+  return r;
+}
+__device__ __forceinline__ void step_release(int* p, int v) {
+  asm volatile("st.release.cta.shared::cta.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int step_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+// wait until *ctr >= target (bounded); false when the limit ran out
+__device__ __forceinline__ bool step_wait(const int* ctr, int target) {
+  if (step_acquire(ctr) >= target) return true;
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    __nanosleep(32);
+    if (step_acquire(ctr) >= target) return true;
+    uint64_t t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (t1 - t0 > kClusterWaitNs) return false;
+  }
+}
+
+constexpr int kPanelCWarps = 4;                                   // critical warps
+constexpr int kPanelCThreads = 32 * kPanelCWarps;                 // 128
+constexpr int kPanelBThreads = kPanelThreads - kPanelCThreads;    // 384 bulk threads
+constexpr int kBarC = 1, kBarB = 2;                               // named barriers of the groups
+constexpr int kStepAbort = 1 << 30;                               // C's step counter after an abort
+
 __global__ void __launch_bounds__(kPanelThreads, 1)
     panel_kernel(int n, int k0, int bb, int rp, double* __restrict__ W, int* __restrict__ posrow,
                  double* __restrict__ Lbuf, double* __restrict__ Mbuf, int* __restrict__ prow_ids,
@@ -116,24 +166,35 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   PanelCand* slots = reinterpret_cast<PanelCand*>(smem);  // [kSlots][cs]
   PanelCand* stage = slots + kSlots * cs;
   double* Wp = reinterpret_cast<double*>(stage + 1);       // [bb][ldp], column-major over own rows
-  double* lrow = Wp + (size_t)ldp * bb;                    // eq. 15 multiplier of the current step
-  int* posl = reinterpret_cast<int*>(lrow + rp);
+  double* lrow = Wp + (size_t)ldp * bb;                    // [2][rp]: eq. 15 multipliers of steps t, t - 1
+  int* posl = reinterpret_cast<int*>(lrow + 2 * rp);
   int* act = posl + rp;                                    // local indices of the active rows
   __shared__ __align__(8) uint64_t slot_bar[kSlots];
-  __shared__ uint64_t red_v[kPanelWarps];
-  __shared__ int red_k[kPanelWarps], red_i[kPanelWarps], wcount[kPanelWarps];
+  __shared__ uint64_t red_v[kPanelCWarps];
+  __shared__ int red_k[kPanelCWarps], red_i[kPanelCWarps], wcount[kPanelWarps];
   __shared__ int s_nact;
+  __shared__ int s_cdone, s_bdone;   // steps whose column t + 1 (C) / bulk update (B) is done
+  __shared__ volatile int s_abort;   // C gave up (timeout or failed step)
+  __shared__ int s_bgo, s_cok;
+  __shared__ int s_win[2];           // slot index (sq * cs + winner) of step t, at t & 1
+  __shared__ int s_cand[2];          // local row of the CTA's step-(t + 1) candidate (-1: none), at t & 1
   const uint32_t rec_bytes = (uint32_t)(cs * sizeof(PanelCand));
   // |v| <= tau  <=>  bits(|v|) <= bits(tau) for non-negative binary64 (tau >= 0)
   const uint64_t tau_bits = static_cast<uint64_t>(__double_as_longlong(tau));
 
-  if (*status != GJ_OK) return;  // an earlier step failed (uniform over the cluster)
+  __shared__ int s_skip;  // rank 0's reading of the call's status (an earlier step failed)
 
   if (tid == 0) {
     for (int q = 0; q < kSlots; ++q) bar_init(&slot_bar[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int q = 0; q < kSlots; ++q) bar_expect(&slot_bar[q], rec_bytes);  // phase 0 of every slot
     s_nact = 0;
+    s_cdone = 0;
+    s_bdone = 0;
+    s_abort = 0;
+    // the status can change while the cluster starts (an update on another stream may fail
+    // it): rank 0 reads it once and every CTA follows rank 0's reading
+    s_skip = (rank == 0) ? (*status != GJ_OK) : 0;
   }
   for (int il = tid; il < rp; il += kPanelThreads) {
     const int g = panel_row(il, rank, cs);
@@ -165,160 +226,244 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   }
   const int nact = s_nact;
   cluster.sync();  // every CTA has armed its slots before any remote store
-
-  // Reduce the per-warp candidates, build the record of the CTA's candidate for step
-  // (k0 + tt) from column tt and store it into every CTA's slot `slot`.  With pend, the
-  // candidate row has a pending eq. 15 update of the previous step (multiplier lrow,
-  // row prow_prev, pivot column tprev) that is applied to its columns on the fly.
-  auto push_candidate = [&](uint64_t bv, int bk, int bi, int tt, int slot, bool pend, const double* prow_prev,
-                            int tprev) {
-    warp_argmax3(bv, bk, bi);
-    if (lane == 0) {
-      red_v[wid] = bv;
-      red_k[wid] = bk;
-      red_i[wid] = bi;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      uint64_t v = (lane < kPanelWarps) ? red_v[lane] : 0ull;
-      int key = (lane < kPanelWarps) ? red_k[lane] : kNoKey;
-      int il = (lane < kPanelWarps) ? red_i[lane] : -1;
-      warp_argmax3(v, key, il);
-      double q = 0.0, inv_q = 0.0;
-      if (il >= 0) {
-        const double l = pend ? lrow[il] : 0.0;
-        q = Wp[il + tt * ldp];  // column tt is already up to date
-        if (lane == 0) inv_q = 1.0 / q;
-        inv_q = __shfl_sync(0xffffffffu, inv_q, 0);
-        for (int j = lane; j < bb; j += 32) {
-          double x = Wp[il + j * ldp];
-          if (pend && j != tt) x = fma(-l, prow_prev[j], (j == tprev) ? 0.0 : x);
-          stage->prow[j] = (j == tt) ? inv_q : x * inv_q;
-        }
-      }
-      if (lane == 0) {
-        stage->absv = v;
-        stage->key = key;
-        stage->row = (il >= 0) ? panel_row(il, rank, cs) : -1;
-        stage->q = q;
-        stage->inv_q = inv_q;
-      }
-    }
-    __syncthreads();
-    if (wid < cs) {  // warp w stores the staged record into CTA w's slot
-      const uint32_t dst = map_rank(smem_addr(&slots[slot * cs + rank]), wid);
-      const uint32_t rbar = map_rank(smem_addr(&slot_bar[slot]), wid);
-      const int4* src4 = reinterpret_cast<const int4*>(stage);
-      constexpr int kWords = sizeof(PanelCand) / sizeof(int4);
-      for (int w = lane; w < kWords; w += 32) st_async16(dst + 16u * w, src4[w], rbar);
-    }
-  };
-
-  {  // step 0 candidates from the panel as loaded
-    uint64_t bv = 0;
-    int bk = kNoKey, bi = -1;
-    for (int a = tid; a < nact; a += kPanelThreads) {
-      const int il = act[a], p = posl[il];
-      if (mode == GJ_PIVOT_NONE ? (p == k0) : (p >= k0)) consider3(Wp[il], p, il, bv, bk, bi);
-    }
-    push_candidate(bv, bk, bi, 0, 0, false, nullptr, 0);
+  if (ld_cluster_s32(map_rank(smem_addr(&s_skip), 0))) {
+    cluster.sync();  // rank 0 stays until every CTA has read its flag
+    return;
   }
 
-  int failed = 0;
-  for (int t = 0; t < bb; ++t) {
-    const int k = k0 + t;
-    const int sq = t % kSlots;
-    // all candidates of step t are in slot sq once its phase t / kSlots completes
-    const bool got = bar_wait(&slot_bar[sq], (uint32_t)((t / kSlots) & 1));
-    if (__syncthreads_or(!got)) {
-      if (tid == 0) {
-        atomicExch(status, GJ_ERR_TIMEOUT);
-        *fail_step = k;
+  if (tid < kPanelCThreads) {
+    // ================================================================ critical warps
+    // Reduce the C threads' candidates to the CTA's candidate for step (k0 + tt) (a row whose
+    // column tt is current), build its record and store it into every CTA's slot `slot`.
+    // For tt > 0 the candidate row still lacks the eq. 15 update of step tprev = tt - 1 on
+    // its columns other than tt (multiplier lpend, row prow_prev); the record applies it on
+    // the fly and writes the updated values back, except on columns tt and tt + 1, which C
+    // handles itself -- so B's step tprev, released here, skips that row.  The record may
+    // read the row only once B has finished step tprev - 1 (bulk_needed steps done).
+    auto push_candidate = [&](uint64_t bv, int bk, int bi, int tt, int slot, const double* lpend,
+                              const double* prow_prev, int bulk_needed) -> bool {
+      const bool pend = tt > 0;
+      const int tprev = tt - 1;
+      warp_argmax3(bv, bk, bi);
+      if (lane == 0) {
+        red_v[wid] = bv;
+        red_k[wid] = bk;
+        red_i[wid] = bi;
       }
-      failed = 1;
-      break;
-    }
-    if (tid == 0 && t + kSlots < bb) bar_expect(&slot_bar[sq], rec_bytes);  // next use of this slot
-    const PanelCand* sl = &slots[sq * cs];
-    uint64_t av[16];
-    int ak[16];
-#pragma unroll
-    for (int c2 = 0; c2 < 16; ++c2) {  // independent loads first
-      av[c2] = (c2 < cs) ? sl[c2].absv : 0ull;
-      ak[c2] = (c2 < cs) ? sl[c2].key : kNoKey;
-    }
-    int ws = 0;
-    uint64_t wv = av[0];
-    int wk = ak[0];
-#pragma unroll
-    for (int c2 = 1; c2 < 16; ++c2)
-      if (key_better(av[c2], ak[c2], wv, wk)) {
-        wv = av[c2];
-        wk = ak[c2];
-        ws = c2;
+      if (tid == 0) s_cok = (bulk_needed <= 0) ? 1 : (int)step_wait(&s_bdone, bulk_needed);
+      group_sync(kBarC, kPanelCThreads);
+      if (!s_cok) return false;  // uniform: read after the barrier
+      if (wid == 0) {
+        uint64_t v = (lane < kPanelCWarps) ? red_v[lane] : 0ull;
+        int key = (lane < kPanelCWarps) ? red_k[lane] : kNoKey;
+        int il = (lane < kPanelCWarps) ? red_i[lane] : -1;
+        warp_argmax3(v, key, il);
+        if (pend && lane == 0) {
+          s_cand[tprev & 1] = il;
+          step_release(&s_cdone, tt);  // B may run step tprev (skipping row il)
+        }
+        double q = 0.0, inv_q = 0.0;
+        if (il >= 0) {
+          const double l = pend ? lpend[il] : 0.0;
+          q = Wp[il + tt * ldp];  // column tt is already up to date
+          if (lane == 0) inv_q = 1.0 / q;
+          inv_q = __shfl_sync(0xffffffffu, inv_q, 0);
+          for (int j = lane; j < bb; j += 32) {
+            double x = Wp[il + j * ldp];
+            if (pend && j != tt) {
+              x = fma(-l, prow_prev[j], (j == tprev) ? 0.0 : x);
+              if (j != tt + 1) Wp[il + j * ldp] = x;  // B's step tprev for this row
+            }
+            stage->prow[j] = (j == tt) ? inv_q : x * inv_q;
+          }
+        }
+        if (lane == 0) {
+          stage->absv = v;
+          stage->key = key;
+          stage->row = (il >= 0) ? panel_row(il, rank, cs) : -1;
+          stage->q = q;
+          stage->inv_q = inv_q;
+        }
       }
-    const PanelCand& win = sl[ws];
-    int st = GJ_OK;
-    if (win.row < 0) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
-    else if (wv >= kInfBits) st = GJ_NONFINITE;
-    else if (wv <= tau_bits) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
-    if (st != GJ_OK) {
+      group_sync(kBarC, kPanelCThreads);
+      for (int dst_rank = wid; dst_rank < cs; dst_rank += kPanelCWarps) {  // warp w stores into CTAs w, w + 4, ...
+        const uint32_t dst = map_rank(smem_addr(&slots[slot * cs + rank]), dst_rank);
+        const uint32_t rbar = map_rank(smem_addr(&slot_bar[slot]), dst_rank);
+        const int4* src4 = reinterpret_cast<const int4*>(stage);
+        constexpr int kWords = sizeof(PanelCand) / sizeof(int4);
+        for (int w = lane; w < kWords; w += 32) st_async16(dst + 16u * w, src4[w], rbar);
+      }
+      return true;
+    };
+
+    bool abort = false;
+    {  // step 0 candidates from the panel as loaded
+      uint64_t bv = 0;
+      int bk = kNoKey, bi = -1;
+      for (int a = tid; a < nact; a += kPanelCThreads) {
+        const int il = act[a], p = posl[il];
+        if (mode == GJ_PIVOT_NONE ? (p == k0) : (p >= k0)) consider3(Wp[il], p, il, bv, bk, bi);
+      }
+      push_candidate(bv, bk, bi, 0, 0, nullptr, nullptr, 0);
+    }
+    const double* prow_prev = nullptr;  // eq. 14 row of step t - 1
+    int R_prev = -1;                    // pivot row of step t - 1
+    for (int t = 0; t < bb; ++t) {
+      const int k = k0 + t;
+      const int sq = t % kSlots;
+      // all candidates of step t are in slot sq once its phase t / kSlots completes
+      const bool got = bar_wait(&slot_bar[sq], (uint32_t)((t / kSlots) & 1));
+      if (group_any(kBarC, kPanelCThreads, !got)) {
+        if (tid == 0) {
+          atomicExch(status, GJ_ERR_TIMEOUT);
+          *fail_step = k;
+        }
+        abort = true;
+        break;
+      }
+      if (tid == 0 && t + kSlots < bb) bar_expect(&slot_bar[sq], rec_bytes);  // next use of this slot
+      const PanelCand* sl = &slots[sq * cs];
+      // lane c reads CTA c's candidate; a shuffle argmax gives every C warp the same winner
+      uint64_t wv = (lane < cs) ? sl[lane].absv : 0ull;
+      int wk = (lane < cs) ? sl[lane].key : kNoKey;
+      int ws = lane;
+      warp_argmax3(wv, wk, ws);
+      // keys of real candidates are distinct; only empty ones tie, and lanes may then hold
+      // different tied slots: every lane takes lane 0's (slot 0 when all are empty)
+      wv = __shfl_sync(0xffffffffu, wv, 0);
+      wk = __shfl_sync(0xffffffffu, wk, 0);
+      ws = __shfl_sync(0xffffffffu, ws, 0);
+      const PanelCand& win = sl[ws];
+      int st = GJ_OK;
+      if (win.row < 0) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+      else if (wv >= kInfBits) st = GJ_NONFINITE;
+      else if (wv <= tau_bits) st = (mode == GJ_PIVOT_NONE) ? GJ_ZERO_PIVOT : GJ_SINGULAR;
+      if (st != GJ_OK) {
+        if (rank == 0 && tid == 0) {
+          *status = st;
+          *fail_step = k;
+        }
+        abort = true;
+        break;
+      }
+      const int rpos = wk, R = win.row;
       if (rank == 0 && tid == 0) {
-        *status = st;
-        *fail_step = k;
+        pivots[k] = win.q;
+        piv_rows[k] = rpos;
+        prow_ids[t] = R;
       }
-      failed = 1;
-      break;
-    }
-    const int rpos = wk, R = win.row;
-    if (rank == 0 && tid == 0) {
-      pivots[k] = win.q;
-      piv_rows[k] = rpos;
-      prow_ids[t] = R;
-    }
-    const bool next = t + 1 < bb;
-    // part 1: interchange (positions), multipliers, column t+1, next candidates
-    uint64_t bv = 0;
-    int bk = kNoKey, bi = -1;
-    for (int a = tid; a < nact; a += kPanelThreads) {
-      const int il = act[a];
-      const int g = panel_row(il, rank, cs);
-      int p = posl[il];
-      if (g == R) {
-        p = k;
-        lrow[il] = 0.0;
-        if (next) Wp[il + (t + 1) * ldp] = win.prow[t + 1];
-      } else {
-        if (p == k) p = rpos;
-        const double l = Wp[il + t * ldp];
-        lrow[il] = l;
-        if (next) {
-          const double nv = fma(-l, win.prow[t + 1], Wp[il + (t + 1) * ldp]);
-          Wp[il + (t + 1) * ldp] = nv;
-          if (mode == GJ_PIVOT_NONE ? (p == k + 1) : (p >= k + 1)) consider3(nv, p, il, bv, bk, bi);
+      const bool next = t + 1 < bb;
+      double* lcur = lrow + (t & 1) * rp;
+      const double* lprev = lrow + ((t + 1) & 1) * rp;
+      // interchange (positions), multipliers of step t, column t + 1 through step t, next
+      // candidates
+      uint64_t bv = 0;
+      int bk = kNoKey, bi = -1;
+      const double pr_t = win.prow[next ? t + 1 : t];
+      const double pr_p = (t > 0 && next) ? prow_prev[t + 1] : 0.0;
+      // four active rows per pass, their loads issued together
+      for (int a0 = tid; a0 < nact; a0 += 4 * kPanelCThreads) {
+        int il[4], g[4];
+        double wt[4], wn[4], lp[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int a = a0 + q * kPanelCThreads;
+          il[q] = (a < nact) ? act[a] : -1;
+          g[q] = (il[q] >= 0) ? panel_row(il[q], rank, cs) : -1;
+          wt[q] = (il[q] >= 0) ? Wp[il[q] + t * ldp] : 0.0;  // column t: current through step t - 1
+          wn[q] = (il[q] >= 0 && next) ? Wp[il[q] + (t + 1) * ldp] : 0.0;  // column t + 1: through t - 2
+          lp[q] = (il[q] >= 0 && t > 0) ? lprev[il[q]] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (il[q] < 0) continue;
+          int p = posl[il[q]];
+          if (g[q] == R) {
+            p = k;
+            lcur[il[q]] = 0.0;
+            if (next) Wp[il[q] + (t + 1) * ldp] = pr_t;
+          } else {
+            if (p == k) p = rpos;
+            lcur[il[q]] = wt[q];
+            if (next) {
+              const double base = (t == 0) ? wn[q] : (g[q] == R_prev) ? pr_p : fma(-lp[q], pr_p, wn[q]);
+              const double nv = fma(-wt[q], pr_t, base);
+              Wp[il[q] + (t + 1) * ldp] = nv;
+              if (mode == GJ_PIVOT_NONE ? (p == k + 1) : (p >= k + 1)) consider3(nv, p, il[q], bv, bk, bi);
+            }
+          }
+          posl[il[q]] = p;
         }
       }
-      posl[il] = p;
-    }
-    if (next) push_candidate(bv, bk, bi, t + 1, (t + 1) % kSlots, true, win.prow, t);
-    // part 2: eq. 14 / eq. 15 on the remaining columns while the candidates travel
-    for (int a = tid; a < nact; a += kPanelThreads) {
-      const int il = act[a];
-      const int g = panel_row(il, rank, cs);
-      if (g == R) {
-        for (int j = 0; j < bb; ++j)
-          if (j != t + 1) Wp[il + j * ldp] = win.prow[j];
+      if (tid == 0) s_win[t & 1] = sq * cs + ws;
+      if (next) {
+        // the barrier inside makes column t + 1, lcur and s_win visible before B is released
+        if (!push_candidate(bv, bk, bi, t + 1, (t + 1) % kSlots, lcur, win.prow, t)) {
+          if (tid == 0) {
+            atomicExch(status, GJ_ERR_TIMEOUT);
+            *fail_step = k;
+          }
+          abort = true;
+          break;
+        }
       } else {
-        const double l = lrow[il];
-        for (int j = 0; j < bb; ++j) {
-          if (j == t + 1) continue;
-          const double base = (j == t) ? 0.0 : Wp[il + j * ldp];
-          Wp[il + j * ldp] = fma(-l, win.prow[j], base);
+        group_sync(kBarC, kPanelCThreads);
+        if (tid == 0) {
+          s_cand[t & 1] = -1;
+          step_release(&s_cdone, t + 1);  // B may run the last step
         }
       }
+      prow_prev = win.prow;
+      R_prev = R;
+    }
+    if (abort && tid == 0) {
+      s_abort = 1;
+      step_release(&s_cdone, kStepAbort);  // releases B from its wait
+    }
+  } else {
+    // ================================================================ bulk warps
+    const int btid = tid - kPanelCThreads;
+    for (int s = 0; s < bb; ++s) {
+      if (btid == 0) s_bgo = step_wait(&s_cdone, s + 1) && !s_abort;
+      group_sync(kBarB, kPanelBThreads);
+      if (!s_bgo) break;  // uniform
+      const PanelCand& win = slots[s_win[s & 1]];
+      const double* lcur = lrow + (s & 1) * rp;
+      const int skip_il = s_cand[s & 1];  // the candidate row: C applied this step to it
+      // local index of the pivot row of step s if this CTA owns it (block-cyclic rows)
+      const int R = win.row, rb = R / kRowBlock;
+      const int pil = (rb % cs == rank) ? (rb / cs) * kRowBlock + (R % kRowBlock) : -1;
+      // eq. 14 (pivot row) / eq. 15 (other active rows) of step s on the columns other than
+      // s + 1 and s + 2; column s becomes the D column of the compact array
+      // one active row per thread and pass, four columns at a time with every load issued
+      // before the dependent FMAs (shared-memory stores would otherwise serialise them)
+      for (int a = btid; a < nact; a += kPanelBThreads) {
+        const int il = act[a];
+        if (il == skip_il) continue;
+        const bool piv = il == pil;
+        const double l = lcur[il];
+        double* wr = Wp + il;
+        for (int j0 = 0; j0 < bb; j0 += 4) {
+          double w[4], pj[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            pj[q] = (j < bb) ? win.prow[j] : 0.0;
+            w[q] = (j < bb && j != s && j != s + 1 && j != s + 2) ? wr[j * ldp] : 0.0;  // C owns s + 1, s + 2
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            if (j < bb && j != s + 1 && j != s + 2) wr[j * ldp] = piv ? pj[q] : fma(-l, pj[q], w[q]);
+          }
+        }
+      }
+      group_sync(kBarB, kPanelBThreads);
+      if (btid == 0) step_release(&s_bdone, s + 1);
     }
   }
   __syncthreads();
+  const bool failed = s_abort != 0;
 
   if (!failed) {
     for (int e = tid; e < nact * bb; e += kPanelThreads) {
@@ -846,7 +991,8 @@ static size_t choose_panel(int64_t n, int want_b, int* cs_out, int* b_out, int* 
 }
 
 gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int pivot_mode, double tau, int panel,
-                      int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs, int lookahead) {
+                      int update, int slices, const CtaOut& out, cudaStream_t s, const Rhs* rhs, int lookahead,
+                      int update_sms) {
   if (n64 > 46340) return GJ_ERR_UNSUPPORTED;
   const int n = (int)n64;
   const int64_t m = rhs ? rhs->m : 0;
@@ -1030,7 +1176,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
     GJ_CUDA(cudaStreamWaitEvent(sb, se.ev_a, 0));
     // SMs left to sb: the cluster's plus room for its fix-ups and narrow updates (3.5
     // cluster sizes measured best at n = 8192, the two streams then take about as long)
-    const int wide_ctas = std::max(1, sms - std::min((7 * cs) / 2, sms / 2));
+    const int wide_ctas = update_sms > 0 ? std::min(update_sms, sms) : std::max(1, sms - std::min((7 * cs) / 2, sms / 2));
     struct Pending {
       bool valid = false;
       int K0 = 0, BB = 0, skip = 0;

@@ -254,3 +254,22 @@ extern "C" gj_status gj_invert_mixed(int64_t n, const float* A, int64_t lda, dou
   cleanup();
   return result;
 }
+
+extern "C" gj_status gj_invert_mixed_prec(int64_t n, const float* A, int64_t lda, double* X, int prec, double tol,
+                                          int max_iter, double* resid_out, int* iters_out, int* rung_out,
+                                          int* det_sign, double* det_log2, void* stream) {
+  // digit slices of the first inverse's update for each named arithmetic
+  int x0;
+  switch (prec) {
+    case GJ_PREC_FP64: x0 = kFp64Slices; break;
+    case GJ_PREC_BF16: x0 = 1; break;
+    case GJ_PREC_FP16: x0 = 2; break;
+    case GJ_PREC_SPLIT_BF16_3: x0 = 2; break;
+    case GJ_PREC_TF32x3: x0 = 3; break;
+    default:
+      set_last_error("gj_invert_mixed_prec: unknown gj_prec value");
+      return GJ_ERR_ARG;
+  }
+  return gj_invert_mixed(n, A, lda, X, x0, 4, tol, max_iter, resid_out, iters_out, rung_out, det_sign, det_log2,
+                         stream);
+}

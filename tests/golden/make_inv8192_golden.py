@@ -11,7 +11,8 @@ few minutes for it, too long for a test, so this script runs it once and stores:
     (the eq. 13 factors) and the relative gap between the best and second-best candidate;
   * det A as sign and log2|det| (eq. 13);
   * 16 whole columns and 16 whole rows of A^-1 at seeded random indices, and 4096
-    single entries at seeded random (row, column) pairs.
+    single entries at seeded random (row, column) pairs;
+  * max |x_ij|, the 1-norm and the Frobenius norm of A^-1 (for the tolerances).
 
 Only the oracle and the seeded input generator are called.  Run from the repository root:
 
@@ -80,6 +81,8 @@ def main() -> None:
         pairs=pairs,
         X_pairs=X[pairs[:, 0], pairs[:, 1]],
         X_absmax=np.array([np.max(np.abs(X))]),
+        X_norm1=np.array([np.max(np.sum(np.abs(X), axis=0))]),
+        X_normF=np.array([np.linalg.norm(X)]),
     )
     meta = {
         "_source": "Written by tests/golden/make_inv8192_golden.py with the FP64 CPU oracle (oracle/gj_oracle.c: "

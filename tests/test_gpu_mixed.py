@@ -73,3 +73,24 @@ def test_mixed_reports_nonconvergence():
     A32 = wl.svd_conditioned(n, 1e2, seed=78, dtype=np.float32)
     r = gj.invert_mixed(torch.from_numpy(np.asfortranarray(A32)).cuda(), x0_slices=3, tol=1e-30, max_iter=3)
     assert r["status"] == gj.NOT_CONVERGED and r["resid"] < 1e-13
+
+
+@pytest.mark.parametrize("prec", [gj.PREC_FP64, gj.PREC_BF16, gj.PREC_FP16, gj.PREC_SPLIT_BF16_3, gj.PREC_TF32x3])
+def test_mixed_prec_names_the_slice_counts(prec):
+    """gj_invert_mixed_prec is gj_invert_mixed with the documented slice count of each gj_prec
+    value: bitwise the same X, residual, rung and determinant."""
+    n = 260
+    A32 = wl.svd_conditioned(n, 1e3, seed=90, dtype=np.float32)
+    dA = torch.from_numpy(np.asfortranarray(A32)).cuda()
+    a = gj.invert_mixed_prec(dA, prec, tol=1e-12)
+    b = gj.invert_mixed(dA, x0_slices=gj.PREC_SLICES[prec], corr_slices=4, tol=1e-12)
+    assert a["status"] == b["status"] == 0
+    assert torch.equal(a["X"], b["X"])
+    for k in ("resid", "iters", "rung", "det_sign", "det_log2"):
+        assert a[k] == b[k], k
+
+
+def test_mixed_prec_rejects_unknown_value():
+    dA = torch.zeros((4, 4), dtype=torch.float32, device="cuda").t()  # column-major
+    with pytest.raises(gj.GJError):
+        gj.invert_mixed_prec(dA, 5)
