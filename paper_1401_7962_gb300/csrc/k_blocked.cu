@@ -57,7 +57,8 @@ struct PanelSmem {
     size_t s = sizeof(PanelCand) * (size_t)(kSlots * cs + 1);
     s += sizeof(double) * (size_t)(rp + 1) * bb;  // Wp, leading dimension rp + 1
     s += sizeof(double) * (size_t)rp * 2;         // lrow (two steps)
-    s += sizeof(int) * (size_t)rp * 2;            // posl, act
+    s += sizeof(double) * (size_t)bb * bb;        // hist: the pivot block's LU factors, step by step
+    s += sizeof(int) * (size_t)rp * 3;            // posl, act, pstep
     return (s + 15) & ~size_t(15);
   }
 };
@@ -76,6 +77,25 @@ __device__ __forceinline__ void consider3(double v, int key, int il, uint64_t& b
   }
 }
 
+// As warp_argmax3, carrying the candidate's value and the reciprocal of it along.
+__device__ __forceinline__ void warp_argmax5(uint64_t& v, int& key, int& il, double& q, double& inv_q) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int ok = __shfl_xor_sync(0xffffffffu, key, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, il, off);
+    const double oq = __shfl_xor_sync(0xffffffffu, q, off);
+    const double oinv = __shfl_xor_sync(0xffffffffu, inv_q, off);
+    if (key_better(ov, ok, v, key)) {
+      v = ov;
+      key = ok;
+      il = oi;
+      q = oq;
+      inv_q = oinv;
+    }
+  }
+}
+
 __device__ __forceinline__ void warp_argmax3(uint64_t& v, int& key, int& il) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -90,24 +110,31 @@ __device__ __forceinline__ void warp_argmax3(uint64_t& v, int& key, int& il) {
   }
 }
 
-// Panel of columns [k0, k0+bb) reduced by one cluster of `cs` CTAs.  Only the rows not yet
-// pivoted when the panel starts ("active" rows: position >= k0) are eliminated step by
-// step -- the pivot search needs nothing else; the rows pivoted earlier end the panel at
-// -N M^-1 (N their panel values at the start, M^-1 the panel's pivot block at the end) and
-// get that from fixup_used_rows_kernel on the whole GPU afterwards.
+// Panel of columns [k0, k0+bb) searched for its pivots by one cluster of `cs` CTAs.  The
+// cluster runs eqs. 14-15 only as far as the pivots and the pivot block need them.  The
+// rows not yet pivoted when the panel starts ("active" rows: position >= k0) are eliminated
+// step by step on the panel columns right of the current one (what the next pivot searches
+// read); their columns left of it keep their eq. 15 multipliers.  A row that becomes a pivot
+// row gets its full compact row (eq. 14 with the D columns of the steps before it, formed
+// from its multipliers and the earlier eq. 14 rows when it is sent as a candidate) and is
+// then updated on every column, so that the pivot rows end as M^-1 (M: their panel values
+// at the start).  Every other row, pivoted earlier or not, ends the panel at -N M^-1 with N
+// its panel values at the start: one product afterwards on the whole GPU (the fix-up).  The
+// cluster writes the pivot record, the positions and the pivot rows' panel columns (M^-1);
+// the other rows of W are left as they were.
 //
 // Each CTA splits its warps in two groups.  The critical warps (C, warps 0-3) carry the
 // chain that decides the pivots: step t waits on the CTA's own mbarrier for the candidates
 // of all CTAs, takes the same winner everywhere, applies the eq. 15 update of steps t - 1
 // and t to column t + 1 of the active rows, finds the CTA's candidate for step t + 1 and
 // stores it with its eq. 14 row into every CTA's shared memory (st.async, counted on the
-// receiver's mbarrier of that slot).  The bulk warps (B, warps 4-15) apply eq. 14 / eq. 15
-// of step s to the other columns one step behind, while C runs the exchange of the next
-// step: step s skips column s + 1 (C already applied steps s - 1 and s to it) and column
-// s + 2 (C applies steps s and s + 1 to it in step s + 1).  Two shared-memory step counters
-// (release / acquire) order the groups: B starts step s once C has finished column s + 1 of
-// step s; C builds the record of its step-(t + 1) candidate only once B has finished step
-// t - 1 (the record applies step t to the candidate row on the fly).  There is no
+// receiver's mbarrier of that slot).  The bulk warps (B, warps 4-15) apply eq. 15 of step
+// s to the columns right of s + 2 one step behind, while C runs the exchange of the next
+// step (column s + 1 has steps s - 1 and s from C already, column s + 2 gets steps s and
+// s + 1 from C in step s + 1).  Two shared-memory step counters (release / acquire) order
+// the groups: B starts step s once C has finished column s + 1 of step s; C builds the
+// record of its step-(t + 1) candidate only once B has finished step t - 1 (the record
+// applies step t to the candidate row on the fly and writes it back).  There is no
 // cluster-wide barrier per step: three slots guarantee that a slot is only rewritten after
 // every CTA has finished the step that read it (B included: a CTA pushes its step-(t + 1)
 // candidate only after its B has finished step t - 1).  Every wait is bounded.
@@ -154,9 +181,8 @@ constexpr int kStepAbort = 1 << 30;                               // C's step co
 
 __global__ void __launch_bounds__(kPanelThreads, 1)
     panel_kernel(int n, int k0, int bb, int rp, double* __restrict__ W, int* __restrict__ posrow,
-                 double* __restrict__ Lbuf, double* __restrict__ Mbuf, int* __restrict__ prow_ids,
-                 double* __restrict__ pivots, int* __restrict__ piv_rows, int32_t* status, int64_t* fail_step,
-                 int mode, double tau) {
+                 double* __restrict__ Mbuf, int* __restrict__ prow_ids, double* __restrict__ pivots,
+                 int* __restrict__ piv_rows, int32_t* status, int64_t* fail_step, int mode, double tau) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int cs = (int)cluster.num_blocks();
@@ -167,10 +193,13 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   PanelCand* stage = slots + kSlots * cs;
   double* Wp = reinterpret_cast<double*>(stage + 1);       // [bb][ldp], column-major over own rows
   double* lrow = Wp + (size_t)ldp * bb;                    // [2][rp]: eq. 15 multipliers of steps t, t - 1
-  int* posl = reinterpret_cast<int*>(lrow + 2 * rp);
+  double* hist = lrow + 2 * rp;                            // [bb][bb]: record row of step s at hist[s * bb]
+  int* posl = reinterpret_cast<int*>(hist + (size_t)bb * bb);
   int* act = posl + rp;                                    // local indices of the active rows
+  int* pstep = act + rp;                                   // step at which a row became a pivot (bb: not yet)
   __shared__ __align__(8) uint64_t slot_bar[kSlots];
   __shared__ uint64_t red_v[kPanelCWarps];
+  __shared__ double red_q[kPanelCWarps], red_inv[kPanelCWarps];
   __shared__ int red_k[kPanelCWarps], red_i[kPanelCWarps], wcount[kPanelWarps];
   __shared__ int s_nact;
   __shared__ int s_cdone, s_bdone;   // steps whose column t + 1 (C) / bulk update (B) is done
@@ -178,7 +207,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   __shared__ int s_bgo, s_cok;
   __shared__ int s_win[2];           // slot index (sq * cs + winner) of step t, at t & 1
   __shared__ int s_cand[2];          // local row of the CTA's step-(t + 1) candidate (-1: none), at t & 1
-  const uint32_t rec_bytes = (uint32_t)(cs * sizeof(PanelCand));
+  __shared__ int s_prow_g[kPanelMaxB];  // pivot row of step t
+  // a record carries its header and the bb entries of prow (rounded up to pairs)
+  const uint32_t rec_bytes = (uint32_t)(cs * (32 + 16 * ((bb + 1) / 2)));
   // |v| <= tau  <=>  bits(|v|) <= bits(tau) for non-negative binary64 (tau >= 0)
   const uint64_t tau_bits = static_cast<uint64_t>(__double_as_longlong(tau));
 
@@ -199,6 +230,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   for (int il = tid; il < rp; il += kPanelThreads) {
     const int g = panel_row(il, rank, cs);
     posl[il] = (g < n) ? posrow[g] : -1;
+    pstep[il] = bb;
   }
   for (int e = tid; e < rp * bb; e += kPanelThreads) {
     const int j = e / rp, il = e - j * rp;
@@ -249,49 +281,89 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
         red_v[wid] = bv;
         red_k[wid] = bk;
         red_i[wid] = bi;
+        // the warp's candidate value (column tt of its row, written by a lane of this warp)
+        // and its reciprocal, formed while the barrier below waits for the bulk warps
+        const double q = (bi >= 0) ? Wp[bi + tt * ldp] : 0.0;
+        red_q[wid] = q;
+        red_inv[wid] = (bi >= 0) ? 1.0 / q : 0.0;
       }
       if (tid == 0) s_cok = (bulk_needed <= 0) ? 1 : (int)step_wait(&s_bdone, bulk_needed);
       group_sync(kBarC, kPanelCThreads);
       if (!s_cok) return false;  // uniform: read after the barrier
-      if (wid == 0) {
-        uint64_t v = (lane < kPanelCWarps) ? red_v[lane] : 0ull;
-        int key = (lane < kPanelCWarps) ? red_k[lane] : kNoKey;
-        int il = (lane < kPanelCWarps) ? red_i[lane] : -1;
-        warp_argmax3(v, key, il);
-        if (pend && lane == 0) {
-          s_cand[tprev & 1] = il;
-          step_release(&s_cdone, tt);  // B may run step tprev (skipping row il)
-        }
-        double q = 0.0, inv_q = 0.0;
-        if (il >= 0) {
-          const double l = pend ? lpend[il] : 0.0;
-          q = Wp[il + tt * ldp];  // column tt is already up to date
-          if (lane == 0) inv_q = 1.0 / q;
-          inv_q = __shfl_sync(0xffffffffu, inv_q, 0);
-          for (int j = lane; j < bb; j += 32) {
-            double x = Wp[il + j * ldp];
-            if (pend && j != tt) {
-              x = fma(-l, prow_prev[j], (j == tprev) ? 0.0 : x);
-              if (j != tt + 1) Wp[il + j * ldp] = x;  // B's step tprev for this row
-            }
-            stage->prow[j] = (j == tt) ? inv_q : x * inv_q;
+      // every C warp reduces the four warps' candidates: all C threads know the CTA's one
+      uint64_t v = (lane < kPanelCWarps) ? red_v[lane] : 0ull;
+      int key = (lane < kPanelCWarps) ? red_k[lane] : kNoKey;
+      int il = (lane < kPanelCWarps) ? red_i[lane] : -1;
+      double q = (lane < kPanelCWarps) ? red_q[lane] : 0.0;
+      double inv_q = (lane < kPanelCWarps) ? red_inv[lane] : 0.0;
+      warp_argmax5(v, key, il, q, inv_q);
+      il = __shfl_sync(0xffffffffu, il, 0);
+      v = __shfl_sync(0xffffffffu, v, 0);
+      key = __shfl_sync(0xffffffffu, key, 0);
+      q = __shfl_sync(0xffffffffu, q, 0);
+      inv_q = __shfl_sync(0xffffffffu, inv_q, 0);
+      if (pend && tid == 0) {
+        s_cand[tprev & 1] = il;
+        step_release(&s_cdone, tt);  // B may run step tprev (skipping row il)
+      }
+      // Every C warp forms the record in registers (lane j: entry j, and j + 32 of a 64-wide
+      // panel) and stores it into the CTAs w, w + 4, ... (st.async of 16-byte pairs); only
+      // warp 0 writes the candidate's step-tprev values back.  Left of tt the candidate holds
+      // its eq. 15 multipliers l_j (it is not a pivot row); the record carries them, so that
+      // the records of the panel's steps together are the LU factors of the pivot block.
+      double pv[2] = {0.0, 0.0};
+      if (il >= 0) {
+        const double l = pend ? lpend[il] : 0.0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = lane + 32 * h;
+          if (j >= bb) continue;
+          double x = Wp[il + j * ldp];
+          if (j < tt) {
+            pv[h] = x;
+            continue;
           }
-        }
-        if (lane == 0) {
-          stage->absv = v;
-          stage->key = key;
-          stage->row = (il >= 0) ? panel_row(il, rank, cs) : -1;
-          stage->q = q;
-          stage->inv_q = inv_q;
+          if (pend && j > tt) {
+            x = fma(-l, prow_prev[j], x);
+            if (wid == 0 && j > tt + 1) Wp[il + j * ldp] = x;  // B's step tprev for this row
+          }
+          pv[h] = (j == tt) ? inv_q : x * inv_q;
         }
       }
-      group_sync(kBarC, kPanelCThreads);
-      for (int dst_rank = wid; dst_rank < cs; dst_rank += kPanelCWarps) {  // warp w stores into CTAs w, w + 4, ...
+      // 16-byte words of the record: 0 = (absv, key, row), 1 = (q, inv_q), 2 + m = prow[2m..2m+1]
+      const int npairs = (bb + 1) >> 1;
+      const int nwords = 2 + npairs;
+      int4 wrd[2];
+      // entry j lives in lane j & 31, in pv[0] for j < 32 and pv[1] above (the receiving lane
+      // picks the half: a shuffle returns the source lane's value of the variable it names)
+      auto entry = [&](int j) -> double {
+        const double lo = __shfl_sync(0xffffffffu, pv[0], j & 31);
+        const double hi = (bb > 32) ? __shfl_sync(0xffffffffu, pv[1], j & 31) : 0.0;
+        return (j >= 32) ? hi : lo;
+      };
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = lane + 32 * h - 2;  // prow pair of word lane + 32 h
+        const double e0 = entry(2 * m), e1 = entry(2 * m + 1);
+        const long long b0 = __double_as_longlong(e0), b1 = __double_as_longlong(e1);
+        wrd[h] = make_int4((int)b0, (int)(b0 >> 32), (int)b1, (int)(b1 >> 32));
+      }
+      if (lane == 0) {
+        const long long av = (long long)v;
+        wrd[0] = make_int4((int)av, (int)(av >> 32), key, (il >= 0) ? panel_row(il, rank, cs) : -1);
+      } else if (lane == 1) {
+        const long long bq = __double_as_longlong((il >= 0) ? q : 0.0);
+        const long long bi2 = __double_as_longlong((il >= 0) ? inv_q : 0.0);
+        wrd[0] = make_int4((int)bq, (int)(bq >> 32), (int)bi2, (int)(bi2 >> 32));
+      }
+      for (int dst_rank = wid; dst_rank < cs; dst_rank += kPanelCWarps) {
         const uint32_t dst = map_rank(smem_addr(&slots[slot * cs + rank]), dst_rank);
         const uint32_t rbar = map_rank(smem_addr(&slot_bar[slot]), dst_rank);
-        const int4* src4 = reinterpret_cast<const int4*>(stage);
-        constexpr int kWords = sizeof(PanelCand) / sizeof(int4);
-        for (int w = lane; w < kWords; w += 32) st_async16(dst + 16u * w, src4[w], rbar);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int w = lane + 32 * h;
+          if (w < nwords) st_async16(dst + 16u * w, wrd[h], rbar);
+        }
       }
       return true;
     };
@@ -307,7 +379,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       push_candidate(bv, bk, bi, 0, 0, nullptr, nullptr, 0);
     }
     const double* prow_prev = nullptr;  // eq. 14 row of step t - 1
-    int R_prev = -1;                    // pivot row of step t - 1
     for (int t = 0; t < bb; ++t) {
       const int k = k0 + t;
       const int sq = t % kSlots;
@@ -369,6 +440,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
         for (int q = 0; q < 4; ++q) {
           const int a = a0 + q * kPanelCThreads;
           il[q] = (a < nact) ? act[a] : -1;
+          if (il[q] >= 0 && pstep[il[q]] < t) il[q] = -1;  // pivot rows of earlier steps are done
           g[q] = (il[q] >= 0) ? panel_row(il[q], rank, cs) : -1;
           wt[q] = (il[q] >= 0) ? Wp[il[q] + t * ldp] : 0.0;  // column t: current through step t - 1
           wn[q] = (il[q] >= 0 && next) ? Wp[il[q] + (t + 1) * ldp] : 0.0;  // column t + 1: through t - 2
@@ -380,13 +452,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
           int p = posl[il[q]];
           if (g[q] == R) {
             p = k;
-            lcur[il[q]] = 0.0;
-            if (next) Wp[il[q] + (t + 1) * ldp] = pr_t;
+            pstep[il[q]] = t;  // the pivot row leaves the elimination
           } else {
             if (p == k) p = rpos;
             lcur[il[q]] = wt[q];
             if (next) {
-              const double base = (t == 0) ? wn[q] : (g[q] == R_prev) ? pr_p : fma(-lp[q], pr_p, wn[q]);
+              const double base = (t == 0) ? wn[q] : fma(-lp[q], pr_p, wn[q]);
               const double nv = fma(-wt[q], pr_t, base);
               Wp[il[q] + (t + 1) * ldp] = nv;
               if (mode == GJ_PIVOT_NONE ? (p == k + 1) : (p >= k + 1)) consider3(nv, p, il[q], bv, bk, bi);
@@ -395,7 +466,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
           posl[il[q]] = p;
         }
       }
-      if (tid == 0) s_win[t & 1] = sq * cs + ws;
+      if (tid == 0) {
+        s_win[t & 1] = sq * cs + ws;
+        s_prow_g[t] = R;
+      }
+      for (int j = tid; j < bb; j += kPanelCThreads) hist[t * bb + j] = win.prow[j];
       if (next) {
         // the barrier inside makes column t + 1, lcur and s_win visible before B is released
         if (!push_candidate(bv, bk, bi, t + 1, (t + 1) % kSlots, lcur, win.prow, t)) {
@@ -414,7 +489,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
         }
       }
       prow_prev = win.prow;
-      R_prev = R;
     }
     if (abort && tid == 0) {
       s_abort = 1;
@@ -431,30 +505,27 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       const double* lcur = lrow + (s & 1) * rp;
       const int skip_il = s_cand[s & 1];  // the candidate row: C applied this step to it
       // local index of the pivot row of step s if this CTA owns it (block-cyclic rows)
-      const int R = win.row, rb = R / kRowBlock;
-      const int pil = (rb % cs == rank) ? (rb / cs) * kRowBlock + (R % kRowBlock) : -1;
-      // eq. 14 (pivot row) / eq. 15 (other active rows) of step s on the columns other than
-      // s + 1 and s + 2; column s becomes the D column of the compact array
       // one active row per thread and pass, four columns at a time with every load issued
       // before the dependent FMAs (shared-memory stores would otherwise serialise them)
       for (int a = btid; a < nact; a += kPanelBThreads) {
         const int il = act[a];
-        if (il == skip_il) continue;
-        const bool piv = il == pil;
+        if (il == skip_il || pstep[il] <= s) continue;  // pivot rows are done
+        // only the columns right of s + 2 (the next pivot searches read them); the columns
+        // left of those keep the row's multipliers
         const double l = lcur[il];
         double* wr = Wp + il;
-        for (int j0 = 0; j0 < bb; j0 += 4) {
+        for (int j0 = s + 3; j0 < bb; j0 += 4) {
           double w[4], pj[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int j = j0 + q;
             pj[q] = (j < bb) ? win.prow[j] : 0.0;
-            w[q] = (j < bb && j != s && j != s + 1 && j != s + 2) ? wr[j * ldp] : 0.0;  // C owns s + 1, s + 2
+            w[q] = (j < bb) ? wr[j * ldp] : 0.0;
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int j = j0 + q;
-            if (j < bb && j != s + 1 && j != s + 2) wr[j * ldp] = piv ? pj[q] : fma(-l, pj[q], w[q]);
+            if (j < bb) wr[j * ldp] = fma(-l, pj[q], w[q]);
           }
         }
       }
@@ -466,45 +537,69 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
   const bool failed = s_abort != 0;
 
   if (!failed) {
-    for (int e = tid; e < nact * bb; e += kPanelThreads) {
-      const int j = e / nact, a = e - j * nact;
-      const int il = act[a];
-      const int g = panel_row(il, rank, cs);
-      const double v = Wp[il + j * ldp];
-      W[(int64_t)g + (int64_t)(k0 + j) * n] = v;
-      Lbuf[(int64_t)g + (int64_t)j * n] = (posl[il] == k0 + j) ? v - 1.0 : v;
-    }
     for (int a = tid; a < nact; a += kPanelThreads) {
       const int il = act[a];
-      const int p = posl[il];
-      posrow[panel_row(il, rank, cs)] = p;
-      if (p >= k0 && p < k0 + bb)  // a pivot row of this panel: its row of M^-1
-        for (int j = 0; j < bb; ++j) Mbuf[(p - k0) * kPanelMaxB + j] = Wp[il + j * ldp];
+      posrow[panel_row(il, rank, cs)] = posl[il];
+    }
+    // The pivot block: M = Lt D U with (from the records) Lt[t][s] = l_s(t) / q_s unit lower,
+    // D = diag(q_t) and U[t][j] = prow_t[j] unit upper; the rows of the pivot rows end the
+    // panel as M^-1 (the compact inverse of M).  Column j of M^-1 solves M x = e_j: forward
+    // substitution with Lt, the scaling by 1 / q_t, back substitution with U.  Warp w of CTA
+    // `rank` takes the columns j = rank + cs (w + 16 m); lane t holds x_t (and x_{t + 32}).
+    for (int j = rank + cs * wid; j < bb; j += cs * kPanelWarps) {
+      double x0 = 0.0, x1 = 0.0;  // rows lane, lane + 32
+      const int t0 = lane, t1 = lane + 32;
+      if (t0 == j) x0 = 1.0;
+      if (t1 == j) x1 = 1.0;
+      for (int s2 = j; s2 < bb; ++s2) {  // forward: y_t -= Lt[t][s2] y_s2 for t > s2
+        const double ys = __shfl_sync(0xffffffffu, s2 < 32 ? x0 : x1, s2 & 31);
+        const double inv_qs = hist[s2 * bb + s2];
+        if (t0 > s2 && t0 < bb) x0 = fma(-(hist[t0 * bb + s2] * inv_qs), ys, x0);
+        if (t1 > s2 && t1 < bb) x1 = fma(-(hist[t1 * bb + s2] * inv_qs), ys, x1);
+      }
+      if (t0 < bb) x0 *= hist[t0 * bb + t0];
+      if (t1 < bb) x1 *= hist[t1 * bb + t1];
+      for (int s2 = bb - 1; s2 > 0; --s2) {  // back: z_t -= U[t][s2] x_s2 for t < s2
+        const double xs = __shfl_sync(0xffffffffu, s2 < 32 ? x0 : x1, s2 & 31);
+        if (t0 < s2) x0 = fma(-hist[t0 * bb + s2], xs, x0);
+        if (t1 < s2) x1 = fma(-hist[t1 * bb + s2], xs, x1);
+      }
+      if (t0 < bb) {
+        W[(int64_t)s_prow_g[t0] + (int64_t)(k0 + j) * n] = x0;
+        Mbuf[t0 * kPanelMaxB + j] = x0;
+      }
+      if (t1 < bb) {
+        W[(int64_t)s_prow_g[t1] + (int64_t)(k0 + j) * n] = x1;
+        Mbuf[t1 * kPanelMaxB + j] = x1;
+      }
     }
   }
   cluster.sync();  // no CTA leaves while stores into its shared memory may be in flight
 }
 
-// Rows pivoted before the panel (position < k0): L[i, :] <- -W[i, P] M^-1 with
-// M^-1[s, t] = Mbuf[s * 64 + t] (the panel's pivot block, written by the panel); these rows
-// are not pivot rows of the panel.  Block (x, y) takes 64 consecutive rows and the 8 columns
-// 8y .. 8y + 7 of the result, so that the FP64 work spreads over as many SMs as the rows
-// allow; the rows' panel values are staged in shared memory with coalesced loads, thread
-// (r, q) forms row r, columns 8y + 2q and 8y + 2q + 1.  Blocks of the same rows read W[i, P]
-// while others write their results, so the results go to L only; fixup_store_kernel then
-// copies them into W[i, P].
+// The rows that are not pivot rows of the panel (position outside [k0, k0 + bb)): the
+// panel leaves them at L[i, :] = -W[i, P] M^-1, with W[i, P] their panel values at the start
+// of the panel (the cluster kernel writes only the pivot rows back) and
+// M^-1[s, t] = Mbuf[s * 64 + t] (the panel's pivot block, written by the panel).  FP64
+// version (the FP64-FMA update path): block (x, y) takes 64 consecutive rows and the 8
+// columns 8y .. 8y + 7 of the result, so that the FP64 work spreads over as many SMs as the
+// rows allow; the rows' panel values are staged in shared memory with coalesced loads,
+// thread (r, q) forms row r, columns 8y + 2q and 8y + 2q + 1.  Blocks of the same rows read
+// W[i, P] while others write their results, so the results go to L only;
+// fixup_store_kernel then copies them into W[i, P].
 constexpr int kFixRows = 64, kFixCols = 8;
-__global__ void __launch_bounds__(256) fixup_used_rows_kernel(int n, int k0, int bb, double* __restrict__ W,
-                                                              const int* __restrict__ posrow,
-                                                              const double* __restrict__ Mbuf,
-                                                              double* __restrict__ Lbuf, const int32_t* status) {
-  if (*status != GJ_OK || k0 == 0) return;
+__device__ __forceinline__ bool panel_pivot_row(int pos, int k0, int bb) { return pos >= k0 && pos < k0 + bb; }
+
+__global__ void __launch_bounds__(256) fixup_rows_kernel(int n, int k0, int bb, double* __restrict__ W,
+                                                         const int* __restrict__ posrow,
+                                                         const double* __restrict__ Mbuf,
+                                                         double* __restrict__ Lbuf, const int32_t* status) {
+  if (*status != GJ_OK) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int r0 = blockIdx.x * kFixRows, t0 = blockIdx.y * kFixCols;
   const int r = tid % kFixRows, q = tid / kFixRows;  // row in the block, column pair
   const int i = r0 + r;
-  const bool used = i < n && posrow[i] < k0;
-  if (!__syncthreads_or(used)) return;  // no row of this block was pivoted earlier
+  const bool other = i < n && !panel_pivot_row(posrow[i], k0, bb);
   __shared__ double Minv[kPanelMaxB][kFixCols];
   __shared__ double Nt[kPanelMaxB][kFixRows + 1];  // Nt[s][r] = W[r0 + r, k0 + s]
   for (int e = tid; e < bb * kFixCols; e += blockDim.x) {
@@ -525,20 +620,35 @@ __global__ void __launch_bounds__(256) fixup_used_rows_kernel(int n, int k0, int
     acc0 = fma(a, Minv[s2][2 * q], acc0);
     acc1 = fma(a, Minv[s2][2 * q + 1], acc1);
   }
-  if (!used) return;
+  if (!other) return;
   const int ta = t0 + 2 * q;
   if (ta < bb) Lbuf[(int64_t)i + (int64_t)ta * n] = -acc0;
   if (ta + 1 < bb) Lbuf[(int64_t)i + (int64_t)(ta + 1) * n] = -acc1;
 }
 
-// W[i, k0 + t] = L[i, t] for the rows pivoted before the panel (the fix-up's results).
+// W[i, k0 + t] = L[i, t] for the rows that are not pivot rows of the panel (the fix-up's
+// results).  With restore_pivots (tensor-core fix-up, which overwrites all of L), the pivot
+// rows' L is put back as their panel values (M^-1) minus 1 at the pivot entry.
 __global__ void fixup_store_kernel(int n, int k0, int bb, double* __restrict__ W, const int* __restrict__ posrow,
-                                   const double* __restrict__ Lbuf, const int32_t* status) {
-  if (*status != GJ_OK || k0 == 0) return;
+                                   double* __restrict__ Lbuf, const int32_t* status, int restore_pivots) {
+  if (*status != GJ_OK) return;
   const int64_t total = (int64_t)n * bb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int t = (int)(e / n), i = (int)(e - (int64_t)t * n);
-    if (posrow[i] < k0) W[(int64_t)i + (int64_t)(k0 + t) * n] = Lbuf[e];
+    const int pos = posrow[i];
+    double* w = &W[(int64_t)i + (int64_t)(k0 + t) * n];
+    if (!panel_pivot_row(pos, k0, bb)) *w = Lbuf[e];
+    else if (restore_pivots) Lbuf[e] = (pos == k0 + t) ? *w - 1.0 : *w;
+  }
+}
+
+// U of the tensor-core fix-up product L = W[:, P] U: U[s + t * bb] = -M^-1[s, t].
+__global__ void fixup_u_kernel(int bb, const double* __restrict__ Mbuf, double* __restrict__ U,
+                               const int32_t* status) {
+  if (*status != GJ_OK) return;
+  for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
+    const int t = e / bb, s2 = e - t * bb;
+    U[e] = -Mbuf[s2 * kPanelMaxB + t];
   }
 }
 
@@ -1024,6 +1134,8 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   GJ_WS(prow_ids, (size_t)Bw * 2);  // two buffers: outer panels alternate (look-ahead)
   double* Mbuf;
   GJ_WS(Mbuf, (size_t)kPanelMaxB * kPanelMaxB);
+  double* Ufix;  // U of the tensor-core fix-up, bb x bb
+  GJ_WS(Ufix, (size_t)kPanelMaxB * kPanelMaxB);
   GJ_WS(oz_err, 4);
   void* oz_ws_b = nullptr;  // the second stream's updates (columns of one outer panel)
   if (tc) {
@@ -1100,7 +1212,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
       {
         ProfScope ps(st_, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
         cfg.stream = st_;
-        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Lbuf, Mbuf, pid + (k0 - K0), pivots,
+        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Mbuf, pid + (k0 - K0), pivots,
                                    piv_rows, out.status, out.fail_step, pivot_mode, tau));
       }
       prof_count(1);
@@ -1108,15 +1220,29 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
         gj_status st = after_first();
         if (st != GJ_OK) return st;
       }
-      if (k0 > 0) {
-        ProfScope ps(st_, "fixup_used_rows", 2.0 * k0 * (double)bb * bb, 16.0 * k0 * (double)bb);
-        const dim3 fx_grid((n + kFixRows - 1) / kFixRows, (bb + kFixCols - 1) / kFixCols);
-        fixup_used_rows_kernel<<<fx_grid, 256, 0, st_>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
-        GJ_CUDA(cudaGetLastError());
-        fixup_store_kernel<<<(unsigned)std::min<int64_t>(((int64_t)n * bb + 255) / 256, sms * 8), 256, 0, st_>>>(
-            n, k0, bb, W, posrow, Lbuf, out.status);
-        GJ_CUDA(cudaGetLastError());
-        prof_count(2);
+      {
+        // the rows that are not pivot rows of this sub-panel: L = -W[i, P] M^-1 (their panel
+        // columns at the end of the sub-panel), then into W[i, P]
+        const unsigned st_blocks = (unsigned)std::min<int64_t>(((int64_t)n * bb + 255) / 256, sms * 8);
+        if (tc) {
+          fixup_u_kernel<<<1, 1024, 0, st_>>>(bb, Mbuf, Ufix, out.status);
+          GJ_CUDA(cudaGetLastError());
+          GJ_CUDA(cudaMemsetAsync(Lbuf, 0, sizeof(double) * (size_t)n * bb, st_));
+          gj_status st = ozaki_update(n, bb, bb, W + (size_t)k0 * n, n, nullptr, Ufix, bb, nullptr, 0, 0, Lbuf, n,
+                                      S, ozw, oz_err, out.status, st_, 0, "fixup_tc");
+          if (st != GJ_OK) return st;
+          fixup_store_kernel<<<st_blocks, 256, 0, st_>>>(n, k0, bb, W, posrow, Lbuf, out.status, 1);
+          GJ_CUDA(cudaGetLastError());
+          prof_count(2);
+        } else {
+          ProfScope ps(st_, "fixup_rows", 2.0 * (n - bb) * (double)bb * bb, 16.0 * (n - bb) * (double)bb);
+          const dim3 fx_grid((n + kFixRows - 1) / kFixRows, (bb + kFixCols - 1) / kFixCols);
+          fixup_rows_kernel<<<fx_grid, 256, 0, st_>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
+          GJ_CUDA(cudaGetLastError());
+          fixup_store_kernel<<<st_blocks, 256, 0, st_>>>(n, k0, bb, W, posrow, Lbuf, out.status, 1);
+          GJ_CUDA(cudaGetLastError());
+          prof_count(2);
+        }
       }
       if (BB > bb) {  // the rest of the outer panel
         gj_status st;
