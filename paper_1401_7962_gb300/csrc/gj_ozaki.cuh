@@ -22,9 +22,21 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S);
 // threads so that the updates of several matrices share the SMs with their panel clusters.
 void set_thread_update_cap(int ctas);
 
+// Row and column options of an update, keyed on row positions row_pos[i] (null: none):
+//   - rows with row_pos[i] in [unit_lo, unit_hi) take the row -e_(row_pos[i] - unit_lo) as
+//     their row of L (instead of L's own values);
+//   - the epilogue stores the product into C, instead of adding it, on the rows with
+//     row_pos[i] in [set_row_lo, set_row_hi) and on the columns in [set_col_lo, set_col_hi).
+struct OzEpilogue {
+  const int* row_pos = nullptr;
+  int unit_lo = 0, unit_hi = 0;
+  int set_row_lo = 0, set_row_hi = 0;
+  int set_col_lo = 0, set_col_hi = 0;
+};
+
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
                        int64_t ldc, int S, void* ws, int32_t* err, int32_t* status, cudaStream_t s,
-                       int max_ctas = 0, const char* prof_name = "update_ozaki_tc");
+                       int max_ctas = 0, const char* prof_name = "update_ozaki_tc", OzEpilogue epi = OzEpilogue());
 
 }  // namespace gj

@@ -8,10 +8,9 @@
 // panel, the panel ends as W[p, P] = M^-1 and W[others, P] = -N M^-1 (compact storage
 // of the D columns), and every other column R must become
 //     W[p, R] <- M^-1 W[p, R],     W[others, R] <- W[others, R] - N M^-1 W[p, R].
-// Both are one update W[:, R] += L U with U = W[p, R] taken before the update and
-// L = W[:, P] after the panel except that 1 is subtracted at the pivot entries
-// (so the pivot rows get (M^-1 - I) U + U = M^-1 U).  U is stored with zero columns on
-// P, which leaves the panel columns unchanged by the same update.
+// Both are one product L U with U = W[p, R] taken before the update and L = W[:, P] after
+// the panel: stored on the pivot rows, added to the others.  U is zero on the columns of
+// P, which the update leaves unchanged.
 //
 // Interchanges are implicit (positions, as in the single-CTA kernel); at the end the
 // inverse is gathered as X[i, j] = W[rowat[i], posrow[j]] (reverse-order
@@ -111,17 +110,18 @@ __device__ __forceinline__ void warp_argmax3(uint64_t& v, int& key, int& il) {
 }
 
 // Panel of columns [k0, k0+bb) searched for its pivots by one cluster of `cs` CTAs.  The
-// cluster runs eqs. 14-15 only as far as the pivots and the pivot block need them.  The
-// rows not yet pivoted when the panel starts ("active" rows: position >= k0) are eliminated
-// step by step on the panel columns right of the current one (what the next pivot searches
-// read); their columns left of it keep their eq. 15 multipliers.  A row that becomes a pivot
-// row gets its full compact row (eq. 14 with the D columns of the steps before it, formed
-// from its multipliers and the earlier eq. 14 rows when it is sent as a candidate) and is
-// then updated on every column, so that the pivot rows end as M^-1 (M: their panel values
-// at the start).  Every other row, pivoted earlier or not, ends the panel at -N M^-1 with N
-// its panel values at the start: one product afterwards on the whole GPU (the fix-up).  The
-// cluster writes the pivot record, the positions and the pivot rows' panel columns (M^-1);
-// the other rows of W are left as they were.
+// cluster runs eqs. 14-15 only as far as the pivot search needs them: the rows not yet
+// pivoted when the panel starts ("active" rows: position >= k0) are eliminated step by step
+// on the panel columns right of the current one, their columns left of it keep their eq. 15
+// multipliers, and a row leaves the elimination when it becomes a pivot row.  Each step's
+// record carries the winner's multipliers and its eq. 14 row, so the panel's records are the
+// LU factors of the pivot block M (the pivot rows' panel values at the start).  With them
+// every CTA solves M y = r for some right-hand sides at the end, and the rest is one
+// product on the whole GPU: the pivot rows end as M^-1 (and M^-1 U on the other columns),
+// every other row, pivoted earlier or not, as -N M^-1 with N its panel values at the start
+// (and its eq. 15 update on the other columns).  The cluster writes the pivot record, the
+// positions and the right-hand factor of that product (on the FP64-FMA path: M^-1 into the
+// pivot rows, for the FP64 fix-up); W is otherwise unchanged.
 //
 // Each CTA splits its warps in two groups.  The critical warps (C, warps 0-3) carry the
 // chain that decides the pivots: step t waits on the CTA's own mbarrier for the candidates
@@ -140,6 +140,10 @@ __device__ __forceinline__ void warp_argmax3(uint64_t& v, int& key, int& il) {
 // candidate only after its B has finished step t - 1).  Every wait is bounded.
 __device__ __forceinline__ void group_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// arrive at named barrier `id` (of `count` threads) without waiting for it
+__device__ __forceinline__ void bar_arrive_group(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 // barrier over `count` threads of named barrier `id`, returns whether any of them passed pred != 0
 __device__ __forceinline__ int group_any(int id, int count, int pred) {
@@ -176,13 +180,14 @@ __device__ __forceinline__ bool step_wait(const int* ctr, int target) {
 constexpr int kPanelCWarps = 4;                                   // critical warps
 constexpr int kPanelCThreads = 32 * kPanelCWarps;                 // 128
 constexpr int kPanelBThreads = kPanelThreads - kPanelCThreads;    // 384 bulk threads
-constexpr int kBarC = 1, kBarB = 2;                               // named barriers of the groups
+constexpr int kBarC = 1, kBarB = 2, kBarRec = 3;                  // named barriers of the groups
 constexpr int kStepAbort = 1 << 30;                               // C's step counter after an abort
 
 __global__ void __launch_bounds__(kPanelThreads, 1)
-    panel_kernel(int n, int k0, int bb, int rp, double* __restrict__ W, int* __restrict__ posrow,
-                 double* __restrict__ Mbuf, int* __restrict__ prow_ids, double* __restrict__ pivots,
-                 int* __restrict__ piv_rows, int32_t* status, int64_t* fail_step, int mode, double tau) {
+    panel_kernel(int n, int k0, int bb, int rp, int K0, int BB, double* __restrict__ W, int* __restrict__ posrow,
+                 double* __restrict__ Mbuf, double* __restrict__ Ufix, int* __restrict__ prow_ids,
+                 double* __restrict__ pivots, int* __restrict__ piv_rows, int32_t* status, int64_t* fail_step,
+                 int mode, double tau) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int cs = (int)cluster.num_blocks();
@@ -307,11 +312,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
         step_release(&s_cdone, tt);  // B may run step tprev (skipping row il)
       }
       // Every C warp forms the record in registers (lane j: entry j, and j + 32 of a 64-wide
-      // panel) and stores it into the CTAs w, w + 4, ... (st.async of 16-byte pairs); only
-      // warp 0 writes the candidate's step-tprev values back.  Left of tt the candidate holds
+      // panel) and stores it into the CTAs w, w + 4, ... (st.async of 16-byte pairs); warp 0
+      // writes the candidate's step-tprev values back once all four warps have read the row
+      // (named barrier kBarRec: warps 1-3 arrive without waiting, warp 0 waits).  Left of tt the candidate holds
       // its eq. 15 multipliers l_j (it is not a pivot row); the record carries them, so that
       // the records of the panel's steps together are the LU factors of the pivot block.
-      double pv[2] = {0.0, 0.0};
+      double pv[2] = {0.0, 0.0}, wb[2] = {0.0, 0.0};
       if (il >= 0) {
         const double l = pend ? lpend[il] : 0.0;
 #pragma unroll
@@ -323,11 +329,21 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
             pv[h] = x;
             continue;
           }
-          if (pend && j > tt) {
-            x = fma(-l, prow_prev[j], x);
-            if (wid == 0 && j > tt + 1) Wp[il + j * ldp] = x;  // B's step tprev for this row
-          }
+          if (pend && j > tt) x = fma(-l, prow_prev[j], x);
+          wb[h] = x;
           pv[h] = (j == tt) ? inv_q : x * inv_q;
+        }
+      }
+      if (wid != 0) {
+        bar_arrive_group(kBarRec, kPanelCThreads);
+      } else {
+        group_sync(kBarRec, kPanelCThreads);
+        if (il >= 0 && pend) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j < bb && j > tt + 1) Wp[il + j * ldp] = wb[h];  // B's step tprev for this row
+          }
         }
       }
       // 16-byte words of the record: 0 = (absv, key, row), 1 = (q, inv_q), 2 + m = prow[2m..2m+1]
@@ -542,16 +558,34 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
       posrow[panel_row(il, rank, cs)] = posl[il];
     }
     // The pivot block: M = Lt D U with (from the records) Lt[t][s] = l_s(t) / q_s unit lower,
-    // D = diag(q_t) and U[t][j] = prow_t[j] unit upper; the rows of the pivot rows end the
-    // panel as M^-1 (the compact inverse of M).  Column j of M^-1 solves M x = e_j: forward
-    // substitution with Lt, the scaling by 1 / q_t, back substitution with U.  Warp w of CTA
-    // `rank` takes the columns j = rank + cs (w + 16 m); lane t holds x_t (and x_{t + 32}).
-    for (int j = rank + cs * wid; j < bb; j += cs * kPanelWarps) {
-      double x0 = 0.0, x1 = 0.0;  // rows lane, lane + 32
+    // D = diag(q_t) and U[t][j] = prow_t[j] unit upper.  M y = r is solved for a right-hand
+    // side r by forward substitution with Lt, the scaling by 1 / q_t and back substitution
+    // with U; warp w of CTA `rank` takes the right-hand sides c = rank + cs (w + 16 m), lane
+    // t holds y_t (and y_{t + 32}).
+    //   Ufix == null (FP64 update path): r = e_c, c < bb: the columns of M^-1, written to Mbuf
+    //     and to the pivot rows' panel columns of W (the compact inverse of M).
+    //   Ufix != null (tensor-core path): c runs over the outer panel [K0, K0 + BB); r = e_t for
+    //     the panel's column k0 + t, else the pivot rows' values in column c (U_R), and
+    //     Ufix[:, c] = -y: V = -M^-1 [I | U_R], the right-hand factor of the one product that
+    //     ends the panel on the outer panel's columns.  Its left-hand factor is W[:, P] (the
+    //     panel values at the start) with the pivot row of step t replaced by -e_t: the pivot
+    //     rows are set to M^-1 [I | U_R], the other rows set to -N M^-1 on the panel's columns
+    //     and given their eq. 15 update -N M^-1 U_R on the others.
+    const int nrhs = Ufix ? BB : bb;
+    const int cP = k0 - K0;  // first panel column within the outer panel
+    for (int c = rank + cs * wid; c < nrhs; c += cs * kPanelWarps) {
+      const int e_at = Ufix ? c - cP : c;  // unit right-hand side e_{e_at}, or none
+      const bool unit = e_at >= 0 && e_at < bb;
       const int t0 = lane, t1 = lane + 32;
-      if (t0 == j) x0 = 1.0;
-      if (t1 == j) x1 = 1.0;
-      for (int s2 = j; s2 < bb; ++s2) {  // forward: y_t -= Lt[t][s2] y_s2 for t > s2
+      double x0 = 0.0, x1 = 0.0;  // rows lane, lane + 32
+      if (unit) {
+        if (t0 == e_at) x0 = 1.0;
+        if (t1 == e_at) x1 = 1.0;
+      } else {
+        if (t0 < bb) x0 = W[(int64_t)s_prow_g[t0] + (int64_t)(K0 + c) * n];
+        if (t1 < bb) x1 = W[(int64_t)s_prow_g[t1] + (int64_t)(K0 + c) * n];
+      }
+      for (int s2 = unit ? e_at : 0; s2 < bb; ++s2) {  // forward: y_t -= Lt[t][s2] y_s2 for t > s2
         const double ys = __shfl_sync(0xffffffffu, s2 < 32 ? x0 : x1, s2 & 31);
         const double inv_qs = hist[s2 * bb + s2];
         if (t0 > s2 && t0 < bb) x0 = fma(-(hist[t0 * bb + s2] * inv_qs), ys, x0);
@@ -564,13 +598,18 @@ __global__ void __launch_bounds__(kPanelThreads, 1)
         if (t0 < s2) x0 = fma(-hist[t0 * bb + s2], xs, x0);
         if (t1 < s2) x1 = fma(-hist[t1 * bb + s2], xs, x1);
       }
-      if (t0 < bb) {
-        W[(int64_t)s_prow_g[t0] + (int64_t)(k0 + j) * n] = x0;
-        Mbuf[t0 * kPanelMaxB + j] = x0;
-      }
-      if (t1 < bb) {
-        W[(int64_t)s_prow_g[t1] + (int64_t)(k0 + j) * n] = x1;
-        Mbuf[t1 * kPanelMaxB + j] = x1;
+      if (Ufix) {
+        if (t0 < bb) Ufix[t0 + (int64_t)c * bb] = -x0;
+        if (t1 < bb) Ufix[t1 + (int64_t)c * bb] = -x1;
+      } else {
+        if (t0 < bb) {
+          W[(int64_t)s_prow_g[t0] + (int64_t)(k0 + c) * n] = x0;
+          Mbuf[t0 * kPanelMaxB + c] = x0;
+        }
+        if (t1 < bb) {
+          W[(int64_t)s_prow_g[t1] + (int64_t)(k0 + c) * n] = x1;
+          Mbuf[t1 * kPanelMaxB + c] = x1;
+        }
       }
     }
   }
@@ -626,11 +665,11 @@ __global__ void __launch_bounds__(256) fixup_rows_kernel(int n, int k0, int bb, 
   if (ta + 1 < bb) Lbuf[(int64_t)i + (int64_t)(ta + 1) * n] = -acc1;
 }
 
-// W[i, k0 + t] = L[i, t] for the rows that are not pivot rows of the panel (the fix-up's
-// results).  With restore_pivots (tensor-core fix-up, which overwrites all of L), the pivot
-// rows' L is put back as their panel values (M^-1) minus 1 at the pivot entry.
+// W[i, k0 + t] = L[i, t] for the rows that are not pivot rows of the panel (the FP64
+// fix-up's results); the pivot rows' L is set to their panel values (M^-1, written by the
+// cluster kernel).
 __global__ void fixup_store_kernel(int n, int k0, int bb, double* __restrict__ W, const int* __restrict__ posrow,
-                                   double* __restrict__ Lbuf, const int32_t* status, int restore_pivots) {
+                                   double* __restrict__ Lbuf, const int32_t* status) {
   if (*status != GJ_OK) return;
   const int64_t total = (int64_t)n * bb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -638,17 +677,7 @@ __global__ void fixup_store_kernel(int n, int k0, int bb, double* __restrict__ W
     const int pos = posrow[i];
     double* w = &W[(int64_t)i + (int64_t)(k0 + t) * n];
     if (!panel_pivot_row(pos, k0, bb)) *w = Lbuf[e];
-    else if (restore_pivots) Lbuf[e] = (pos == k0 + t) ? *w - 1.0 : *w;
-  }
-}
-
-// U of the tensor-core fix-up product L = W[:, P] U: U[s + t * bb] = -M^-1[s, t].
-__global__ void fixup_u_kernel(int bb, const double* __restrict__ Mbuf, double* __restrict__ U,
-                               const int32_t* status) {
-  if (*status != GJ_OK) return;
-  for (int e = threadIdx.x; e < bb * bb; e += blockDim.x) {
-    const int t = e / bb, s2 = e - t * bb;
-    U[e] = -Mbuf[s2 * kPanelMaxB + t];
+    else Lbuf[e] = *w;
   }
 }
 
@@ -666,10 +695,13 @@ __global__ void gather_u_kernel(int n, int k0, int bb, int c_lo, int c_hi, const
 }
 
 // W[:, c_lo:c_hi] += L U in FP64 (one FMA per term).  64 x 64 tile per CTA, 4 x 4 per thread.
+// The panel's pivot rows (position in [k0, k0 + bb)) take L U instead (their L is M^-1: eq. 14
+// for them is W[p, R] = M^-1 W[p, R]), outside the panel's own columns.
 constexpr int kTM = 64, kTN = 64, kTK = 32;
 __global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, int c_lo, int c_hi,
                                                           const double* __restrict__ L,
                                                           const double* __restrict__ U, double* __restrict__ W,
+                                                          const int* __restrict__ posrow, int k0,
                                                           const int32_t* status) {
   if (*status != GJ_OK) return;
   __shared__ double Ls[kTK][kTM];
@@ -712,12 +744,18 @@ __global__ void __launch_bounds__(256) update_dfma_kernel(int n, int bb, int c_l
     const int cw = cw0 + ty + 16 * j;
     if (cw >= wn) continue;
     const int c = c_lo + cw;
+    const bool in_panel = c >= k0 && c < k0 + bb;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = m0 + tx + 16 * i;
       if (r < n) {
         double* p = &W[(int64_t)r + (int64_t)c * n];
-        *p = *p + acc[i][j];
+        const int pos = posrow[r];
+        if (pos >= k0 && pos < k0 + bb) {
+          if (!in_panel) *p = acc[i][j];
+        } else {
+          *p = *p + acc[i][j];
+        }
       }
     }
   }
@@ -1134,8 +1172,8 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   GJ_WS(prow_ids, (size_t)Bw * 2);  // two buffers: outer panels alternate (look-ahead)
   double* Mbuf;
   GJ_WS(Mbuf, (size_t)kPanelMaxB * kPanelMaxB);
-  double* Ufix;  // U of the tensor-core fix-up, bb x bb
-  GJ_WS(Ufix, (size_t)kPanelMaxB * kPanelMaxB);
+  double* Ufix;  // V of the tensor-core path's product per sub-panel, bb x (outer panel width)
+  GJ_WS(Ufix, (size_t)kPanelMaxB * 128);
   GJ_WS(oz_err, 4);
   void* oz_ws_b = nullptr;  // the second stream's updates (columns of one outer panel)
   if (tc) {
@@ -1194,7 +1232,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
       // algorithmic work: n x (wn - bb) columns outside the sub-panel, 2 bb FLOP each;
       // bytes: those columns of W read and written once, L and U read once
       ProfScope ps(s, "update_dfma", 2.0 * n * (double)(wn - bb) * bb, 16.0 * n * (double)wn + 16.0 * n * bb);
-      update_dfma_kernel<<<grid, 256, 0, s>>>(n, bb, c_lo, c_hi, Lbuf, U, W, out.status);
+      update_dfma_kernel<<<grid, 256, 0, s>>>(n, bb, c_lo, c_hi, Lbuf, U, W, posrow, k0, out.status);
     }
     GJ_CUDA(cudaGetLastError());
     prof_count(2);
@@ -1212,49 +1250,44 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
       {
         ProfScope ps(st_, "panel_cluster", 2.0 * n * bb * bb, 16.0 * n * bb);
         cfg.stream = st_;
-        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, W, posrow, Mbuf, pid + (k0 - K0), pivots,
-                                   piv_rows, out.status, out.fail_step, pivot_mode, tau));
+        GJ_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, n, k0, bb, rp, K0, BB, W, posrow, Mbuf,
+                                   tc ? Ufix : (double*)nullptr, pid + (k0 - K0), pivots, piv_rows, out.status,
+                                   out.fail_step, pivot_mode, tau));
       }
       prof_count(1);
       if (k0 == K0 && after_first) {
         gj_status st = after_first();
         if (st != GJ_OK) return st;
       }
-      {
-        // the rows that are not pivot rows of this sub-panel: L = -W[i, P] M^-1 (their panel
-        // columns at the end of the sub-panel), then into W[i, P]
-        const unsigned st_blocks = (unsigned)std::min<int64_t>(((int64_t)n * bb + 255) / 256, sms * 8);
-        if (tc) {
-          fixup_u_kernel<<<1, 1024, 0, st_>>>(bb, Mbuf, Ufix, out.status);
-          GJ_CUDA(cudaGetLastError());
-          GJ_CUDA(cudaMemsetAsync(Lbuf, 0, sizeof(double) * (size_t)n * bb, st_));
-          gj_status st = ozaki_update(n, bb, bb, W + (size_t)k0 * n, n, nullptr, Ufix, bb, nullptr, 0, 0, Lbuf, n,
-                                      S, ozw, oz_err, out.status, st_, 0, "fixup_tc");
-          if (st != GJ_OK) return st;
-          fixup_store_kernel<<<st_blocks, 256, 0, st_>>>(n, k0, bb, W, posrow, Lbuf, out.status, 1);
-          GJ_CUDA(cudaGetLastError());
-          prof_count(2);
-        } else {
-          ProfScope ps(st_, "fixup_rows", 2.0 * (n - bb) * (double)bb * bb, 16.0 * (n - bb) * (double)bb);
-          const dim3 fx_grid((n + kFixRows - 1) / kFixRows, (bb + kFixCols - 1) / kFixCols);
-          fixup_rows_kernel<<<fx_grid, 256, 0, st_>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
-          GJ_CUDA(cudaGetLastError());
-          fixup_store_kernel<<<st_blocks, 256, 0, st_>>>(n, k0, bb, W, posrow, Lbuf, out.status, 1);
-          GJ_CUDA(cudaGetLastError());
-          prof_count(2);
-        }
-      }
-      if (BB > bb) {  // the rest of the outer panel
-        gj_status st;
-        if (tc) {
-          // columns [K0, K0 + BB) of W; U = the sub-panel's pivot rows, zero on the sub-panel
-          st = ozaki_update(n, BB, bb, Lbuf, n, nullptr, W + (size_t)K0 * n, n, pid + (k0 - K0), k0 - K0,
-                            k0 - K0 + bb, W + (size_t)K0 * n, n, S, ozw, oz_err, out.status, st_, 0,
-                            "update_ozaki_panel");
-        } else {
-          st = fp64_update(k0, bb, K0, K0 + BB, pid + (k0 - K0));
-        }
+      if (tc) {
+        // the outer panel [K0, K0 + BB): the product L V (V from the cluster, L the panel's
+        // columns as they were at its start, the pivot row of step t replaced by -e_t) is
+        // stored on the pivot rows and on the panel's columns and added elsewhere
+        OzEpilogue pe;
+        pe.row_pos = posrow;
+        pe.unit_lo = pe.set_row_lo = k0;
+        pe.unit_hi = pe.set_row_hi = k0 + bb;
+        pe.set_col_lo = k0 - K0;
+        pe.set_col_hi = k0 - K0 + bb;
+        gj_status st = ozaki_update(n, BB, bb, W + (size_t)k0 * n, n, nullptr, Ufix, bb, nullptr, 0, 0,
+                                    W + (size_t)K0 * n, n, S, ozw, oz_err, out.status, st_, 0, "update_ozaki_panel", pe);
         if (st != GJ_OK) return st;
+      } else {
+        // the rows that are not pivot rows of this sub-panel: L = -W[i, P] M^-1 (their panel
+        // columns at the end of the sub-panel), then into W[i, P]; then the rest of the outer
+        // panel by the FP64 update
+        ProfScope ps(st_, "fixup_rows", 2.0 * (n - bb) * (double)bb * bb, 16.0 * (n - bb) * (double)bb);
+        const unsigned st_blocks = (unsigned)std::min<int64_t>(((int64_t)n * bb + 255) / 256, sms * 8);
+        const dim3 fx_grid((n + kFixRows - 1) / kFixRows, (bb + kFixCols - 1) / kFixCols);
+        fixup_rows_kernel<<<fx_grid, 256, 0, st_>>>(n, k0, bb, W, posrow, Mbuf, Lbuf, out.status);
+        GJ_CUDA(cudaGetLastError());
+        fixup_store_kernel<<<st_blocks, 256, 0, st_>>>(n, k0, bb, W, posrow, Lbuf, out.status);
+        GJ_CUDA(cudaGetLastError());
+        prof_count(2);
+        if (BB > bb) {
+          gj_status st = fp64_update(k0, bb, K0, K0 + BB, pid + (k0 - K0));
+          if (st != GJ_OK) return st;
+        }
       }
     }
     return GJ_OK;
@@ -1263,19 +1296,25 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
   // The rank-BB update of outer panel [K0, K0 + BB) on the columns outside [K0, K0 + skip)
   // (inversion; skip >= BB) or right of K0 + skip (solving).
   auto outer_update = [&](int K0, int BB, int skip, const int* pid, cudaStream_t st_, int max_ctas) -> gj_status {
+    // L = the outer panel's columns (final), U = its pivot rows: stored on the pivot rows
+    // (M^-1 U: eq. 14 for the panel's rows), added on the others (eq. 15)
+    OzEpilogue oe;
+    oe.row_pos = posrow;
+    oe.set_row_lo = K0;
+    oe.set_row_hi = K0 + BB;
     if (!solving) {
       const int zhi = std::min(n, K0 + skip);
       if (K0 == 0 && zhi >= n) return GJ_OK;  // nothing outside
       if (tc)
-        return ozaki_update(n, n, BB, W + (size_t)K0 * n, n, pid, W, n, pid, K0, zhi, W, n, S, oz_ws, oz_err,
-                            out.status, st_, max_ctas, "update_ozaki_wide");
+        return ozaki_update(n, n, BB, W + (size_t)K0 * n, n, nullptr, W, n, pid, K0, zhi, W, n, S, oz_ws, oz_err,
+                            out.status, st_, max_ctas, "update_ozaki_wide", oe);
       return fp64_update(K0, BB, 0, n, pid);
     }
     const int c0 = K0 + skip;
     if (c0 >= nw) return GJ_OK;
     if (tc)
-      return ozaki_update(n, nw - c0, BB, W + (size_t)K0 * n, n, pid, W + (size_t)c0 * n, n, pid, 0, 0,
-                          W + (size_t)c0 * n, n, S, oz_ws, oz_err, out.status, st_, max_ctas, "update_ozaki_wide");
+      return ozaki_update(n, nw - c0, BB, W + (size_t)K0 * n, n, nullptr, W + (size_t)c0 * n, n, pid, 0, 0,
+                          W + (size_t)c0 * n, n, S, oz_ws, oz_err, out.status, st_, max_ctas, "update_ozaki_wide", oe);
     return fp64_update(K0, BB, c0, nw, pid);
   };
 
@@ -1329,8 +1368,12 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
       if (BBn > 0) {
         // narrow update: panel p + 1's columns, after the wide update of panel p - 1
         if (p > 0) GJ_CUDA(cudaStreamWaitEvent(sb, se.ev_a, 0));
-        st = ozaki_update(n, BBn, BB, W + (size_t)K0 * n, n, pid, W + (size_t)K1 * n, n, pid, 0, 0,
-                          W + (size_t)K1 * n, n, S, oz_ws_b, oz_err, out.status, sb, 0, "update_ozaki_panel");
+        OzEpilogue ne;
+        ne.row_pos = posrow;
+        ne.set_row_lo = K0;
+        ne.set_row_hi = K0 + BB;
+        st = ozaki_update(n, BBn, BB, W + (size_t)K0 * n, n, nullptr, W + (size_t)K1 * n, n, pid, 0, 0,
+                          W + (size_t)K1 * n, n, S, oz_ws_b, oz_err, out.status, sb, 0, "update_ozaki_panel", ne);
         if (st != GJ_OK) return st;
       }
       GJ_CUDA(cudaEventRecord(se.ev_b, sb));

@@ -114,7 +114,8 @@ __device__ __forceinline__ void write_digits(__nv_bfloat16* out, int S, int64_t 
 // minus_one_at[k] (optional): subtract 1 from L[minus_one_at[k], k] (the blocked
 // Gauss-Jordan L of the panel: pivot entries minus the identity).
 __device__ __forceinline__ void slice_rows(int warp, int nwarps, int M, int K, const double* __restrict__ L,
-                                           int64_t ldl, const int* __restrict__ minus_one_at, int S, int mpad,
+                                           int64_t ldl, const int* __restrict__ minus_one_at,
+                                           const int* __restrict__ row_pos, int unit_lo, int unit_hi, int S, int mpad,
                                            __nv_bfloat16* __restrict__ out, int* __restrict__ erow) {
   const int lane = threadIdx.x & 31;
   int mo[4];
@@ -126,11 +127,14 @@ __device__ __forceinline__ void slice_rows(int warp, int nwarps, int M, int K, c
   for (int i = warp; i < mpad; i += nwarps) {
     double x[4];
     int e = -100000;
+    const int pos = (row_pos && i < M) ? row_pos[i] : -1;
+    const bool unit = row_pos && pos >= unit_lo && pos < unit_hi;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int k = lane * 4 + q;
       double v = (i < M && k < K) ? L[(int64_t)i + (int64_t)k * ldl] : 0.0;
       if (mo[q] == i) v -= 1.0;
+      if (unit) v = (k == pos - unit_lo) ? -1.0 : 0.0;
       x[q] = v;
       e = max(e, exp_of(v));
     }
@@ -175,14 +179,16 @@ __device__ __forceinline__ void slice_cols(int warp, int nwarps, int N, int K, c
 // One launch slices both operands: blocks [0, row_blocks) take the rows of L, the rest the
 // columns of U.
 __global__ void slice_kernel(int row_blocks, int M, int N, int K, const double* __restrict__ L, int64_t ldl,
-                             const int* __restrict__ minus_one_at, const double* __restrict__ U, int64_t ldu,
+                             const int* __restrict__ minus_one_at, const int* __restrict__ row_pos, int unit_lo,
+                             int unit_hi, const double* __restrict__ U, int64_t ldu,
                              const int* __restrict__ row_ids, int zero_lo, int zero_hi, int S, int mpad, int npad,
                              __nv_bfloat16* __restrict__ As, __nv_bfloat16* __restrict__ Bs, int* __restrict__ erow,
                              int* __restrict__ ecol, const int32_t* status) {
   if (status && *status != GJ_OK) return;
   const int wpb = blockDim.x >> 5;
   if ((int)blockIdx.x < row_blocks) {
-    slice_rows((int)blockIdx.x * wpb + (threadIdx.x >> 5), row_blocks * wpb, M, K, L, ldl, minus_one_at, S, mpad,
+    slice_rows((int)blockIdx.x * wpb + (threadIdx.x >> 5), row_blocks * wpb, M, K, L, ldl, minus_one_at, row_pos,
+               unit_lo, unit_hi, S, mpad,
                As, erow);
   } else {
     const int b = (int)blockIdx.x - row_blocks;
@@ -254,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     ozaki_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                         int N, int mpad, int npad, int S, int nkc, int tiles_m, int tiles_n, int ts_lo, int ts_hi,
                         int skip_lo, int skip_hi, double* __restrict__ C, int64_t ldc, const int* __restrict__ erow,
-                        const int* __restrict__ ecol, int32_t* err, int32_t* status, uint64_t wait_ns) {
+                        const int* __restrict__ ecol, int32_t* err, int32_t* status, uint64_t wait_ns,
+                        OzEpilogue epi) {
   if (status && *status != GJ_OK) return;
   const int tiles_n_act = tiles_n - (ts_hi - ts_lo);
   const int ntiles = tiles_m * tiles_n_act;
@@ -438,6 +445,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       c0 += h * kEpiCols;
       const int gi = m0 + r;
       const bool row_ok = gi < M;
+      // rows whose position is in the set range take the product instead of adding it
+      const int gpos = (epi.row_pos && row_ok) ? epi.row_pos[gi] : -1;
+      const bool set_row = epi.row_pos && gpos >= epi.set_row_lo && gpos < epi.set_row_hi;
       // kCSm of this row's C values into shared memory now (cp.async, overlapping the MMAs);
       // the column exponents of the warp's kEpiCols columns, one per lane
 #pragma unroll
@@ -520,8 +530,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < kB; ++c) {
           const int cl = b * kB + c, gj = c0 + cl;
           const int ec = __shfl_sync(0xffffffffu, ec_lane, cl);
-          if (!row_ok || gj >= N || (gj >= skip_lo && gj < skip_hi) || T[cl] == 0) continue;
-          C[(int64_t)gi + (int64_t)gj * ldc] = cold[b & 1][c] + i64_to_double_pow2(T[cl], er + ec - 55);
+          const bool set = set_row || (gj >= epi.set_col_lo && gj < epi.set_col_hi);
+          if (!row_ok || gj >= N || (gj >= skip_lo && gj < skip_hi) || (T[cl] == 0 && !set)) continue;
+          const double prod = i64_to_double_pow2(T[cl], er + ec - 55);
+          C[(int64_t)gi + (int64_t)gj * ldc] = set ? prod : cold[b & 1][c] + prod;
         }
       }
     }
@@ -614,7 +626,7 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int S) {
 gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl, const int* l_minus_one_at,
                        const double* U, int64_t ldu, const int* u_row_ids, int zero_lo, int zero_hi, double* C,
                        int64_t ldc, int S, void* ws, int32_t* err, int32_t* status, cudaStream_t s,
-                       int max_ctas, const char* prof_name) {
+                       int max_ctas, const char* prof_name, OzEpilogue epi) {
   if (K < 1 || K > kKB || S < 1 || S > 8) return GJ_ERR_ARG;
   if (max_ctas <= 0) max_ctas = t_update_cap;
   const int64_t mpad = (M + kTM - 1) / kTM * kTM, npad = (N + kTM - 1) / kTM * kTM;
@@ -632,7 +644,8 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   // 8 warps per block, one row (column) per warp per pass
   const int sb = (int)std::min<int64_t>((mpad + 7) / 8, (int64_t)sms * 16);
   const int sc = (int)std::min<int64_t>((npad + 7) / 8, (int64_t)sms * 16);
-  slice_kernel<<<sb + sc, 256, 0, s>>>(sb, (int)M, (int)N, K, L, ldl, l_minus_one_at, U, ldu, u_row_ids, zero_lo,
+  slice_kernel<<<sb + sc, 256, 0, s>>>(sb, (int)M, (int)N, K, L, ldl, l_minus_one_at, epi.row_pos, epi.unit_lo,
+                                       epi.unit_hi, U, ldu, u_row_ids, zero_lo,
                                        zero_hi, S, (int)mpad, (int)npad, As, Bs, erow, ecol, status);
   GJ_CUDA(cudaGetLastError());
   prof_count(1);
@@ -665,7 +678,7 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
                  16.0 * (double)M * (double)N);
     ozaki_update_kernel<<<grid, kThreads, smem, s>>>(mapA, mapB, (int)M, (int)N, (int)mpad, (int)npad, S, nkc,
                                                     tiles_m, tiles_n, ts_lo, ts_hi, zero_lo, zero_hi, C, ldc, erow,
-                                                    ecol, err, status, wait_ns);
+                                                    ecol, err, status, wait_ns, epi);
   }
   GJ_CUDA(cudaGetLastError());
   prof_count(1);
