@@ -41,8 +41,10 @@ if ROOT not in sys.path:
 from paper_1401_7962_gb300 import workloads as wl  # noqa: E402
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# Nominal GB300 FP64 rate: 152 SMs x 2 FP64 FMA lanes per clock x 2 FLOP x ~2.06 GHz.
+# Nominal GB300 FP64 rate: 152 SMs x 2 FP64 FMA lanes per clock x 2 FLOP x ~2.06 GHz; used only
+# when the run's own probe (gj_measure_peaks) is not available.
 FP64_NOMINAL_GFLOPS = 1250.0
+PROBED = {}  # this run's gj_measure_peaks result
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel from one ncu capture (profiles/), with the order it was taken at; scaled to the
@@ -218,10 +220,15 @@ def roofline_tensor(tensor_tflops: float, fp64_equiv_tflops, pairs, traffic) -> 
 
 def roofline_fp64(achieved_gflops: float, traffic) -> dict:
     # FP64 FMA is plain ALU work on GB300 (DMMA measures no faster than DFMA), so the
-    # peak is the FP64 unit rate, not a tensor rate.
-    return {"bound": "alu", "achieved": round(achieved_gflops / 1000.0, 4), "peak": FP64_NOMINAL_GFLOPS / 1000.0,
-            "unit": "TFLOP/s", "frac": round(achieved_gflops / FP64_NOMINAL_GFLOPS, 4), "traffic": traffic,
-            "peak_source": "nominal FP64 unit rate (152 SMs x 4 FLOP/clk x 2.06 GHz); DFMA probe measured 1.197"}
+    # peak is the FP64 unit rate, not a tensor rate: this run's DFMA probe when it ran
+    if PROBED.get("fp64_fma_gflops"):
+        peak = PROBED["fp64_fma_gflops"]
+        src = "of measured: FP64 FMA probe (gj_measure_peaks) in this run, independent chains on every SM"
+    else:
+        peak = FP64_NOMINAL_GFLOPS
+        src = "nominal FP64 unit rate (152 SMs x 4 FLOP/clk x 2.06 GHz)"
+    return {"bound": "alu", "achieved": round(achieved_gflops / 1000.0, 4), "peak": round(peak / 1000.0, 4),
+            "unit": "TFLOP/s", "frac": round(achieved_gflops / peak, 4), "traffic": traffic, "peak_source": src}
 
 
 # ----------------------------------------------------------------- CPU oracle legs
@@ -325,6 +332,10 @@ def run_gpu(args) -> None:
     _build.build()
     import paper_1401_7962_gb300 as gj
     L = gj.lib()
+    try:
+        PROBED.update(gj.measure_peaks())
+    except Exception as exc:  # pragma: no cover - reported in the line
+        PROBED["error"] = str(exc)
     line = measure(args, gj, L, dev, world, rank)
     if rank == 0 and world == 1 and args.workload == "inv8192" and not args.n and not args.headline_only:
         subs = {}
@@ -339,11 +350,80 @@ def run_gpu(args) -> None:
             torch.cuda.empty_cache()
             L.gj_trim_memory()
         line["config"]["configs"] = subs
+        line["config"]["panel_sweep"] = panel_sweep(args, gj, L, dev)
+    if rank == 0 and line:
+        line["config"]["peaks_probed"] = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in PROBED.items()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_8192_meta():
+    try:
+        with open(os.path.join(GOLDEN_DIR, "inv8192_partial_oracle.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def oracle_parity_8192(dX, rec) -> dict:
+    """The benchmark's last 8192 inverse against the oracle's stored result for the same input
+    (tests/golden/inv8192_partial_oracle.*): pivot sequence, det, and the largest difference
+    over the 16 stored columns, 16 rows and 4096 entries, relative to max |x| of the oracle's
+    inverse."""
+    meta = golden_8192_meta()
+    if not meta:
+        return {"available": False}
+    ref = np.load(os.path.join(GOLDEN_DIR, "inv8192_partial_oracle.npz"))
+    X = dX.cpu().numpy()
+    cols, rows, pairs = ref["cols"], ref["rows"], ref["pairs"]
+    d = max(np.max(np.abs(X[:, cols] - ref["X_cols"])), np.max(np.abs(X[rows, :] - ref["X_rows"])),
+            np.max(np.abs(X[pairs[:, 0], pairs[:, 1]] - ref["X_pairs"])))
+    out = {"available": True, "max_abs_diff_over_max_x": float(d / ref["X_absmax"][0]),
+           "compared": "16 columns, 16 rows, 4096 entries"}
+    if rec is not None:
+        out["pivots_identical"] = bool(np.array_equal(rec["piv_rows"], ref["piv_rows"]))
+        out["det_sign_equal"] = rec["det_sign"] == meta["det_sign"]
+        out["det_log2_rel_diff"] = abs(rec["det_log2"] - meta["det_log2"]) / abs(meta["det_log2"])
+    return out
+
+
+def panel_sweep(args, gj, L, dev) -> dict:
+    """The 8192 inversion with each cluster panel width the blocked path takes at this order
+    (the tensor-core update's outer panel is 128 columns; a 64-column cluster panel does not
+    fit the shared memory of 16 CTAs at n = 8192): ms per inversion, 3 timed after 2 more."""
+    import ctypes
+    import torch
+    W = WORKLOADS["inv8192"]
+    n = W["n"]
+    dA = torch.from_numpy(wl.gaussian(n, W["seed"], shift=W["shift"] * n)).to(dev)
+    dX = torch.empty_like(dA)
+    stream = torch.cuda.Stream(device=dev)
+    sgn, lg2 = ctypes.c_int(0), ctypes.c_double(0.0)
+    out = {}
+    for b in (16, 32):
+        opts = gj._Opts()
+        opts.stream = stream.cuda_stream
+        opts.panel = b
+        run = lambda: L.gj_invert_ex(ctypes.byref(opts), n, dA.data_ptr(), n, dX.data_ptr(), W["pivot"],
+                                     ctypes.byref(sgn), ctypes.byref(lg2))
+        for _ in range(2):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            run()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        out[f"cluster_panel_{b}"] = {"ms_per_inverse": round(ms, 2), "gflops": round(2.0 * n ** 3 / ms / 1e6, 1)}
+    out["outer_panel"] = 128
+    return out
 
 
 def sub_entry(sub: dict) -> dict:
@@ -634,6 +714,19 @@ def measure(args, gj, L, dev, world: int, rank: int) -> dict:
     if rank == 0 and world == 1 and not args.no_cpu and not args.n and not args.count:
         cpu = cpu_oracle_sample(args.workload)
         cpu.pop("gflops", None)
+        if args.workload == "inv8192":
+            meta = golden_8192_meta()
+            if meta:
+                cpu["full_size_single_core"] = {
+                    "seconds": meta["oracle_seconds"], "gflops": round(2.0 * 8192 ** 3 / meta["oracle_seconds"] / 1e9, 3),
+                    "where": "the x86 development host, one core, when tests/golden/inv8192_partial_oracle.* was "
+                             "written (not this machine; the full-size oracle takes about 11 minutes)"}
+    if rank == 0 and args.workload == "inv8192" and not args.n and args.update != "dfma":
+        # one more inversion (untimed) with the pivot record, in the timed launch configuration
+        rec = gj.invert(dA, W["pivot"], out=dX, record=True, stream=stream, panel=args.panel,
+                        update_sms=args.update_sms)
+        torch.cuda.synchronize(dev)
+        extra["oracle_parity"] = oracle_parity_8192(dX, rec)
 
     if rank == 0:
         cfg = {"workload": W["name"], "pivot": ["none", "partial", "full"][W["pivot"]],

@@ -401,6 +401,22 @@ gj_status gj_trim_memory(void);
  */
 gj_status gj_set_wait_limit_ns(uint64_t ns);
 
+/*
+ * gj_measure_peaks -- arithmetic throughput of the current GPU, measured with probe kernels
+ * of independent chains on every SM (no memory traffic): FP64 FMA, FP64 mma.sync (m8n8k4)
+ * and FP32 FMA, in GFLOP/s (best of five timed launches after a warm-up).  The paper has no
+ * counterpart; these are the denominators of the benchmark's rooflines for FP64 work.
+ * Synchronous; allocates 64 bytes of device memory for the duration of the call.
+ */
+typedef struct gj_peaks {
+  double fp64_fma_gflops;
+  double fp64_mma_gflops;
+  double fp32_fma_gflops;
+  int32_t sm_count;
+  double max_clock_mhz;
+} gj_peaks;
+gj_status gj_measure_peaks(gj_peaks* out);
+
 /* gj_status_string -- static text for a status code. */
 const char* gj_status_string(int status);
 

@@ -43,6 +43,11 @@ class _Opts(ctypes.Structure):
                 ("fail_step", ctypes.c_void_p), ("lookahead", ctypes.c_int32), ("update_sms", ctypes.c_int32)]
 
 
+class _Peaks(ctypes.Structure):
+    _fields_ = [("fp64_fma_gflops", ctypes.c_double), ("fp64_mma_gflops", ctypes.c_double),
+                ("fp32_fma_gflops", ctypes.c_double), ("sm_count", ctypes.c_int32), ("max_clock_mhz", ctypes.c_double)]
+
+
 _LIB = None
 
 
@@ -94,6 +99,8 @@ def lib() -> ctypes.CDLL:
     L.gj_version.argtypes = []
     L.gj_trim_memory.restype = I
     L.gj_trim_memory.argtypes = []
+    L.gj_measure_peaks.restype = I
+    L.gj_measure_peaks.argtypes = [ctypes.POINTER(_Peaks)]
     L.gj_set_wait_limit_ns.restype = I
     L.gj_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
     _LIB = L
@@ -106,6 +113,16 @@ def status_string(status: int) -> str:
 
 def last_error() -> str:
     return lib().gj_last_error().decode()
+
+
+def measure_peaks() -> dict:
+    """``gj_measure_peaks``: measured FP64 FMA, FP64 mma.sync and FP32 FMA rates of the current GPU."""
+    p = _Peaks()
+    st = lib().gj_measure_peaks(ctypes.byref(p))
+    if st != OK:
+        raise GJError(st, "gj_measure_peaks")
+    return {"fp64_fma_gflops": p.fp64_fma_gflops, "fp64_mma_gflops": p.fp64_mma_gflops,
+            "fp32_fma_gflops": p.fp32_fma_gflops, "sm_count": p.sm_count, "max_clock_mhz": p.max_clock_mhz}
 
 
 def set_wait_limit_ns(ns: int) -> None:

@@ -100,3 +100,13 @@ def test_emulated_update_argument_errors():
     assert L_.gj_gemm_update_emulated(4, 4, 4, 1, 4, 1, 4, 1, 4, 9, None) == gj.ERR_ARG
     assert L_.gj_gemm_update_emulated(4, 4, 4, 1, 3, 1, 4, 1, 4, 8, None) == gj.ERR_ARG
     assert L_.gj_gemm_update_emulated(0, 4, 4, 0, 1, 0, 4, 0, 1, 8, None) == gj.OK
+
+
+def test_peak_probes_report_plausible_rates():
+    """gj_measure_peaks (the benchmark's FP64 roofline denominators): finite, positive rates;
+    the FP32 FMA rate well above the FP64 rates on this part."""
+    p = gj.measure_peaks()
+    assert p["sm_count"] > 0 and p["max_clock_mhz"] > 0
+    for k in ("fp64_fma_gflops", "fp64_mma_gflops", "fp32_fma_gflops"):
+        assert np.isfinite(p[k]) and p[k] > 10.0, (k, p[k])
+    assert p["fp32_fma_gflops"] > 4 * p["fp64_fma_gflops"]
