@@ -53,7 +53,9 @@ PROBED = {}  # this run's gj_measure_peaks result
 NCU_TRAFFIC = {
     "update_dfma": None,  # column-window change since profiles/update_dfma_inv6144.md
     # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (96 CTAs)
-    "update_ozaki_wide": None,  # the slicing changed since profiles/ozaki_update_kernel_inv6144.md
+    # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (96 CTAs),
+    # profiles/ozaki_update_kernel_inv6144.md
+    "update_ozaki_wide": {"n": 6144, "bytes": 318.799872e6 + 232.829696e6},
     "update_ozaki_tc": None,
     # the plan replays one kernel per order bin; traffic summed over those kernels
     "batched_plan": None,
