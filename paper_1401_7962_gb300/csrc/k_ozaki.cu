@@ -21,7 +21,7 @@
 //
 // Kernel shape: persistent, one CTA per SM walking 128 x 64 tiles of C.  Warp 0 issues the
 // TMA loads (all S digit slices of the U tile stay resident; the L slices stream through a
-// 2-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), eight
+// 2-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), sixteen
 // warps run the epilogue (TMEM lane = row of the tile).  Every mbarrier wait is bounded in
 // time; on expiry the kernel records an error, drains its own TMA loads and MMAs, frees its
 // tensor memory and returns.
@@ -51,9 +51,13 @@ constexpr int kABox = kTM * kKC * 2;   // 16 KiB: one TMA box (128 rows x 64 k)
 constexpr int kAStage = 2 * kABox;     // 32 KiB: the two boxes of a slice (k 0..63, 64..127)
 constexpr int kBBox = kTN * kKC * 2;   // 8 KiB
 #ifndef GJ_EPI_WARPS
-#define GJ_EPI_WARPS 8
+#define GJ_EPI_WARPS 16
 #endif
-constexpr int kEpiWarps = GJ_EPI_WARPS;  // per TMEM lane quarter kEpiWarps / 4, each with a column slice
+// Per TMEM lane quarter kEpiWarps / 4 warps, each with a column slice.  The epilogue is bound
+// by latency (dependent integer and FP64 chains, TMEM and memory round trips), not by any one
+// pipe: sixteen warps of 16 columns (92 registers) hide it where eight warps of 32 columns
+// (166 registers, the most a 10-warp block gets) left it setting the tile period.
+constexpr int kEpiWarps = GJ_EPI_WARPS;
 constexpr int kEpiSlices = kEpiWarps / 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr int kEpiCols = kTN / kEpiSlices;  // columns per epilogue thread
@@ -246,8 +250,8 @@ struct SmemLayout {
 // in column-major order, so consecutive tiles of a CTA share their U slices, which are
 // loaded again only when the tile column changes.
 // Roles: warp 0 = TMA producer (U slices of a new tile column, then the L slices through the
-// ring), warp 1 = MMA issuer, warps 2-9 = epilogue (warp w reads TMEM lanes
-// 32 (w % 4) .. + 31 and the column half (w - 2) / 4 of the tile).
+// ring), warp 1 = MMA issuer, warps 2 .. kEpiWarps + 1 = epilogue (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 and the column slice (w - 2) / 4 of the tile).
 // The L slices are consumed in ascending order, so digit group g is final once slice g has
 // been consumed (its terms come from slices s <= g): the MMA warp commits group g to its own
 // barrier there, and the epilogue drains the groups one by one while the MMAs of the higher
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..9)
+    // ---------------- epilogue (warps 2 .. kEpiWarps + 1)
     const int q = warp & 3;
     const int h = (warp - 2) >> 2;   // column slice of the tile
     const int r = q * 32 + lane;
