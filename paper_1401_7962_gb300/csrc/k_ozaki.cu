@@ -59,7 +59,15 @@ constexpr int kBBox = kTN * kKC * 2;   // 8 KiB
 // (166 registers, the most a 10-warp block gets) left it setting the tile period.
 constexpr int kEpiWarps = GJ_EPI_WARPS;
 constexpr int kEpiSlices = kEpiWarps / 4;
-constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+// Two threads issue the MMAs, each for its own digit groups (accumulators): the issue of one
+// thread, sharing its SM sub-partition with four epilogue warps, set the MMA rate at this
+// N = 64 shape.  Warp 1 and the last warp issue; they sit on different sub-partitions.
+constexpr int kIssuers = 2;
+constexpr int kIssuerWarp2 = 2 + kEpiWarps;
+constexpr int kThreads = 64 + 32 * kEpiWarps + 32;  // producer warp, MMA warps, epilogue warps
+// digit groups whose MMAs each issuer takes (bit g = group g) when S = 7: 13 and 15 of the 28
+// digit products per term; for other S the groups alternate
+constexpr uint32_t kOwnS7[kIssuers] = {0x47u, 0x38u};
 constexpr int kEpiCols = kTN / kEpiSlices;  // columns per epilogue thread
 constexpr int kCSm = kEpiCols / 2; // of those, prefetched into shared memory (the rest load in the final pass)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: default pipeline wait, and every teardown drain
@@ -239,6 +247,26 @@ __device__ __forceinline__ double i64_to_double_pow2(long long T, int e) {
   return __longlong_as_double(bits + (static_cast<long long>(e) << 52));
 }
 
+// The MMAs of slice SL of a tile for the common case S = 7 digit slices, K = 128 (two TMA
+// boxes per slice), fully unrolled: every accumulator address and descriptor is the slice's
+// base plus a constant.  One thread issues all MMAs of the CTA, and the instructions between
+// two MMAs bound their rate at this N = 64 shape (a loop with run-time bounds issued about
+// one MMA per 80 clocks where the tensor pipe can take one per ~60).  Descriptors hold the
+// shared-memory address in 16-byte units in their low bits, so adding (bytes >> 4) moves them.
+template <int SL, uint32_t OWN>
+__device__ __forceinline__ void mma_slice_s7k2(uint32_t tmem, uint64_t a_stage, uint64_t b_res) {
+#pragma unroll
+  for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+    for (int t = 0; t < 7 - SL; ++t)
+#pragma unroll
+      for (int k16 = 0; k16 < kKC / 16; ++k16)
+        if ((OWN >> (SL + t)) & 1u)
+          tc::mma_bf16(tmem + (uint32_t)(kTN * (SL + t)), a_stage + (uint64_t)((kc * kABox) >> 4) + 2u * k16,
+                     b_res + (uint64_t)(((t * 2 + kc) * kBBox) >> 4) + 2u * k16, kIdesc,
+                     (SL > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
+}
+
 struct SmemLayout {
   static size_t bytes(int S) {
     return 1024 /*align slack*/ + (size_t)S * 2 * kBBox + (size_t)kStages * kAStage +
@@ -287,13 +315,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     tc::mbar_init(&bar_bfull, 1);
-    tc::mbar_init(&bar_bempty, 1);
+    tc::mbar_init(&bar_bempty, kIssuers);
     for (int i = 0; i < kStages; ++i) {
       tc::mbar_init(&bar_full[i], 1);
-      tc::mbar_init(&bar_empty[i], 1);
+      tc::mbar_init(&bar_empty[i], kIssuers);
     }
-    for (int g = 0; g < 8; ++g) tc::mbar_init(&bar_gready[g], 1);
-    tc::mbar_init(&bar_fin, 1);
+    for (int g = 0; g < 8; ++g) tc::mbar_init(&bar_gready[g], kIssuers);
+    tc::mbar_init(&bar_fin, kIssuers);
     tc::fence_mbar_init();
     s_drained = 0;
     s_abort = 0;
@@ -372,9 +400,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == kIssuerWarp2) {
     if (lane == 0) {
-      // ---------------- MMA issuer
+      // ---------------- MMA issuers: the same waits and commits, each its own MMAs
+      const int me = (warp == 1) ? 0 : 1;
       int it = 0, local = 0, b_used = 0;
       for (int idx = t_begin; idx < t_end && !s_abort; ++idx, ++local) {
         bool ok = true;
@@ -396,14 +425,42 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::tc_fence_after();
           // one wait and two commits per slice: all k of the slice against every U slice t
-          for (int kc = 0; kc < nkc; ++kc) {
-            const uint64_t a0 = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kAStage + (size_t)kc * kABox));
-            for (int t = 0; sl + t < S; ++t) {
-              const uint32_t d = tmem + (uint32_t)(kTN * (sl + t));
-              const uint64_t b0 = tc::desc_k128_sw128(tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox));
+          if (S == 7 && nkc == 2) {
+            const uint64_t as = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kAStage));
+            const uint64_t bs = tc::desc_k128_sw128(tc::smem_u32(Bres));
+            if (me == 0) {
+              switch (sl) {
+                case 0: mma_slice_s7k2<0, kOwnS7[0]>(tmem, as, bs); break;
+                case 1: mma_slice_s7k2<1, kOwnS7[0]>(tmem, as, bs); break;
+                case 2: mma_slice_s7k2<2, kOwnS7[0]>(tmem, as, bs); break;
+                case 3: mma_slice_s7k2<3, kOwnS7[0]>(tmem, as, bs); break;
+                case 4: mma_slice_s7k2<4, kOwnS7[0]>(tmem, as, bs); break;
+                case 5: mma_slice_s7k2<5, kOwnS7[0]>(tmem, as, bs); break;
+                default: mma_slice_s7k2<6, kOwnS7[0]>(tmem, as, bs); break;
+              }
+            } else {
+              switch (sl) {
+                case 0: mma_slice_s7k2<0, kOwnS7[1]>(tmem, as, bs); break;
+                case 1: mma_slice_s7k2<1, kOwnS7[1]>(tmem, as, bs); break;
+                case 2: mma_slice_s7k2<2, kOwnS7[1]>(tmem, as, bs); break;
+                case 3: mma_slice_s7k2<3, kOwnS7[1]>(tmem, as, bs); break;
+                case 4: mma_slice_s7k2<4, kOwnS7[1]>(tmem, as, bs); break;
+                case 5: mma_slice_s7k2<5, kOwnS7[1]>(tmem, as, bs); break;
+                default: mma_slice_s7k2<6, kOwnS7[1]>(tmem, as, bs); break;
+              }
+            }
+          } else {
+            for (int kc = 0; kc < nkc; ++kc) {
+              const uint64_t a0 =
+                  tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kAStage + (size_t)kc * kABox));
+              for (int t = 0; sl + t < S; ++t) {
+                if (((sl + t) & 1) != me) continue;
+                const uint32_t d = tmem + (uint32_t)(kTN * (sl + t));
+                const uint64_t b0 = tc::desc_k128_sw128(tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox));
 #pragma unroll
-              for (int k16 = 0; k16 < kKC / 16; ++k16)
-                tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
+                for (int k16 = 0; k16 < kKC / 16; ++k16)
+                  tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
+              }
             }
           }
           if (S < kStages) tc::mma_commit(&bar_empty[stage]);
@@ -558,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (issued_uses[st] > 0 && !tc::mbar_wait(&bar_full[st], (uint32_t)((issued_uses[st] - 1) & 1), kWaitNs))
           atomicExch(err, 41);
     }
-    if (warp == 1 && lane == 0) {
+    if ((warp == 1 || warp == kIssuerWarp2) && lane == 0) {
       tc::mma_commit(&bar_fin);
       if (!tc::mbar_wait(&bar_fin, 0, kWaitNs)) atomicExch(err, 42);
     }
