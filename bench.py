@@ -52,10 +52,9 @@ PROBED = {}  # this run's gj_measure_peaks result
 # when its kernel changes, until it is captured again.
 NCU_TRAFFIC = {
     "update_dfma": None,  # column-window change since profiles/update_dfma_inv6144.md
-    # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (96 CTAs)
-    # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (96 CTAs),
+    # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (104 CTAs),
     # profiles/ozaki_update_kernel_inv6144.md
-    "update_ozaki_wide": {"n": 6144, "bytes": 318.799872e6 + 232.829696e6},
+    "update_ozaki_wide": {"n": 6144, "bytes": 318.940160e6 + 232.985344e6},
     "update_ozaki_tc": None,
     # the plan replays one kernel per order bin; traffic summed over those kernels
     "batched_plan": None,
@@ -648,7 +647,7 @@ def measure(args, gj, L, dev, world: int, rank: int) -> dict:
         if dominant == "update_ozaki_wide" and W.get("n", 0) >= 2048:
             cs = min(16, -(-W["n"] // 256))
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            roof["grid_sms"] = sms - min((7 * cs) // 2, sms // 2)
+            roof["grid_sms"] = min(args.update_sms, sms) if args.update_sms > 0 else sms - min(3 * cs, sms // 2)
             roof["note"] = (f"look-ahead: runs on {roof['grid_sms']} of {sms} SMs while the panel stream reduces "
                             "the next panel; share_of_step counts overlapped time")
     elif dominant in prof and prof[dominant]["launches"]:

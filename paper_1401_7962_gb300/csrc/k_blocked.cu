@@ -1334,7 +1334,7 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
     //   ev_a (s -> sb): wide update of panel p done (panel p + 2's columns current).
     // The wide update is enqueued after the next panel's first cluster, and may not start
     // before the narrow update ends: a 16-CTA cluster needs 16 free SMs of one GPC, which the
-    // wide update's 96 persistent CTAs would otherwise scatter over every GPC for the length
+    // wide update's persistent CTAs would otherwise scatter over every GPC for the length
     // of the launch.  (Letting the wide update start right after the panel's reduction, beside
     // the narrow update, measured 102.8 ms instead of 66.9: the clusters waited for SMs.)
     StreamEvents se;
@@ -1344,9 +1344,10 @@ gj_status run_blocked(int64_t n64, const double* A, int64_t lda, double* X, int 
     cudaStream_t sb = se.sb;
     GJ_CUDA(cudaEventRecord(se.ev_a, s));  // set-up done
     GJ_CUDA(cudaStreamWaitEvent(sb, se.ev_a, 0));
-    // SMs left to sb: the cluster's plus room for its fix-ups and narrow updates (3.5
-    // cluster sizes measured best at n = 8192, the two streams then take about as long)
-    const int wide_ctas = update_sms > 0 ? std::min(update_sms, sms) : std::max(1, sms - std::min((7 * cs) / 2, sms / 2));
+    // SMs left to sb: the cluster's plus room for its narrow updates, three cluster sizes
+    // (the wide update gets 104 of 152: best of 88-120 at n = 8192, 55.4 ms against 57.7 at
+    // 96 and 56.2 at 112; the two streams then take about as long)
+    const int wide_ctas = update_sms > 0 ? std::min(update_sms, sms) : std::max(1, sms - std::min(3 * cs, sms / 2));
     struct Pending {
       bool valid = false;
       int K0 = 0, BB = 0, skip = 0;
