@@ -152,7 +152,8 @@ __device__ __forceinline__ void slice_rows(int warp, int nwarps, int M, int K, c
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
-    write_digits(out, S, (int64_t)mpad * kKB, (int64_t)i * kKB + lane * 4, x, e);
+    // only the k the MMAs read: whole K16 steps up to K (the rest of the row is never read)
+    if (lane * 4 < ((K + 15) & ~15)) write_digits(out, S, (int64_t)mpad * kKB, (int64_t)i * kKB + lane * 4, x, e);
     if (lane == 0) erow[i] = e;
   }
 }
@@ -183,7 +184,7 @@ __device__ __forceinline__ void slice_cols(int warp, int nwarps, int N, int K, c
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
-    write_digits(out, S, (int64_t)npad * kKB, (int64_t)j * kKB + lane * 4, x, e);
+    if (lane * 4 < ((K + 15) & ~15)) write_digits(out, S, (int64_t)npad * kKB, (int64_t)j * kKB + lane * 4, x, e);
     if (lane == 0) ecol[j] = e;
   }
 }
@@ -290,7 +291,7 @@ struct SmemLayout {
 // end-of-tile wait, with the pipe about to drain anyway, did not.)
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
-                        int N, int mpad, int npad, int S, int nkc, int tiles_m, int tiles_n, int ts_lo, int ts_hi,
+                        int N, int mpad, int npad, int S, int nkc, int nk16_last, int tiles_m, int tiles_n, int ts_lo, int ts_hi,
                         int skip_lo, int skip_hi, double* __restrict__ C, int64_t ldc, const int* __restrict__ erow,
                         const int* __restrict__ ecol, int32_t* err, int32_t* status, uint64_t wait_ns,
                         OzEpilogue epi) {
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::tc_fence_after();
           // one wait and two commits per slice: all k of the slice against every U slice t
-          if (S == 7 && nkc == 2) {
+          if (S == 7 && nkc == 2 && nk16_last == kKC / 16) {
             const uint64_t as = tc::desc_k128_sw128(tc::smem_u32(Aring + (size_t)stage * kAStage));
             const uint64_t bs = tc::desc_k128_sw128(tc::smem_u32(Bres));
             if (me == 0) {
@@ -457,9 +458,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (((sl + t) & 1) != me) continue;
                 const uint32_t d = tmem + (uint32_t)(kTN * (sl + t));
                 const uint64_t b0 = tc::desc_k128_sw128(tc::smem_u32(Bres + (size_t)(t * 2 + kc) * kBBox));
+                // the last box holds K - 64 (nkc - 1) of its 64 k: nk16_last K16 steps
+                const int nk16 = (kc == nkc - 1) ? nk16_last : kKC / 16;
 #pragma unroll
                 for (int k16 = 0; k16 < kKC / 16; ++k16)
-                  tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
+                  if (k16 < nk16)
+                    tc::mma_bf16(d, a0 + 2u * k16, b0 + 2u * k16, kIdesc, (sl > 0 || kc > 0 || k16 > 0) ? 1u : 0u);
               }
             }
           }
@@ -719,6 +723,7 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
   const size_t smem = SmemLayout::bytes(S);
   GJ_CUDA(allow_max_dynamic_smem((const void*)ozaki_update_kernel));
   const int nkc = (K + kKC - 1) / kKC;
+  const int nk16_last = (K - (nkc - 1) * kKC + 15) / 16;
   const int tiles_m = (int)((M + kTM - 1) / kTM), tiles_n = (int)((N + kTN - 1) / kTN);
   // column tiles lying wholly inside [zero_lo, zero_hi) receive nothing: not scheduled
   int ts_lo = 0, ts_hi = 0;
@@ -738,7 +743,7 @@ gj_status ozaki_update(int64_t M, int64_t N, int K, const double* L, int64_t ldl
     ProfScope ps(s, prof_name, 0.5 * S * (S + 1) * 2.0 * (double)M * (double)(N - (zero_hi - zero_lo)) * K,
                  16.0 * (double)M * (double)N);
     ozaki_update_kernel<<<grid, kThreads, smem, s>>>(mapA, mapB, (int)M, (int)N, (int)mpad, (int)npad, S, nkc,
-                                                    tiles_m, tiles_n, ts_lo, ts_hi, zero_lo, zero_hi, C, ldc, erow,
+                                                    nk16_last, tiles_m, tiles_n, ts_lo, ts_hi, zero_lo, zero_hi, C, ldc, erow,
                                                     ecol, err, status, wait_ns, epi);
   }
   GJ_CUDA(cudaGetLastError());
