@@ -54,7 +54,7 @@ NCU_TRAFFIC = {
     "update_dfma": None,  # column-window change since profiles/update_dfma_inv6144.md
     # the wide (outer) update of the blocked path, launch 203 of the kernel at n = 6144 (104 CTAs),
     # profiles/ozaki_update_kernel_inv6144.md
-    "update_ozaki_wide": {"n": 6144, "bytes": 318.940160e6 + 232.985344e6},
+    "update_ozaki_wide": {"n": 6144, "bytes": 318.893568e6 + 232.922368e6},
     "update_ozaki_tc": None,
     # the plan replays one kernel per order bin; traffic summed over those kernels
     "batched_plan": None,
