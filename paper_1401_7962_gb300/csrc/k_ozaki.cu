@@ -21,8 +21,9 @@
 //
 // Kernel shape: persistent, one CTA per SM walking 128 x 64 tiles of C.  Warp 0 issues the
 // TMA loads (all S digit slices of the U tile stay resident; the L slices stream through a
-// 2-stage ring), warp 1 issues the MMAs (M = 128, N = 64, K = 16 per instruction), sixteen
-// warps run the epilogue (TMEM lane = row of the tile).  Every mbarrier wait is bounded in
+// 2-stage ring), warp 1 and the last warp issue the MMAs (M = 128, N = 64, K = 16 per
+// instruction), each for its own digit groups, sixteen warps run the epilogue (TMEM lane =
+// row of the tile).  Every mbarrier wait is bounded in
 // time; on expiry the kernel records an error, drains its own TMA loads and MMAs, frees its
 // tensor memory and returns.
 #include <cuda.h>
