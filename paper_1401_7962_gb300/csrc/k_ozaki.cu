@@ -280,16 +280,17 @@ struct SmemLayout {
 // in column-major order, so consecutive tiles of a CTA share their U slices, which are
 // loaded again only when the tile column changes.
 // Roles: warp 0 = TMA producer (U slices of a new tile column, then the L slices through the
-// ring), warp 1 = MMA issuer, warps 2 .. kEpiWarps + 1 = epilogue (warp w reads TMEM lanes
+// ring), warp 1 and warp kIssuerWarp2 = MMA issuers (each for its own digit groups, with the
+// same waits and commits), warps 2 .. kEpiWarps + 1 = epilogue (warp w reads TMEM lanes
 // 32 (w % 4) .. + 31 and the column slice (w - 2) / 4 of the tile).
 // The L slices are consumed in ascending order, so digit group g is final once slice g has
-// been consumed (its terms come from slices s <= g): the MMA warp commits group g to its own
-// barrier there, and the epilogue drains the groups one by one while the MMAs of the higher
-// groups run.  At the end of a tile the MMA warp waits once, on a shared-memory counter, for
-// the epilogue to have read the last group; the epilogue then combines and stores the tile
-// while the next tile's MMAs run.  (Waits of the MMA thread on epilogue-arrived mbarriers in
-// the middle of a tile's MMA stream measured markedly slower MMA issue on GB300; this single
-// end-of-tile wait, with the pipe about to drain anyway, did not.)
+// been consumed (its terms come from slices s <= g): both issuers commit to group g's barrier
+// there (it counts both), and the epilogue drains the groups one by one while the MMAs of the
+// higher groups run.  At the end of a tile each issuer waits once, on a shared-memory counter,
+// for the epilogue to have read the last group; the epilogue then combines and stores the tile
+// while the next tile's MMAs run.  (Waits of an issuer inside a tile's MMA stream, on
+// epilogue-arrived mbarriers or on per-group counters, measured markedly slower MMA issue on
+// GB300; this single end-of-tile wait, with the pipe about to drain anyway, did not.)
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                         int N, int mpad, int npad, int S, int nkc, int nk16_last, int tiles_m, int tiles_n, int ts_lo, int ts_hi,
