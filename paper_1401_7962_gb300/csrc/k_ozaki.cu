@@ -69,6 +69,8 @@ constexpr int kThreads = 64 + 32 * kEpiWarps + 32;  // producer warp, MMA warps,
 // digit groups whose MMAs each issuer takes (bit g = group g) when S = 7: 13 and 15 of the 28
 // digit products per term; for other S the groups alternate
 constexpr uint32_t kOwnS7[kIssuers] = {0x47u, 0x38u};
+static_assert((kOwnS7[0] & kOwnS7[1]) == 0u && (kOwnS7[0] | kOwnS7[1]) == 0x7Fu,
+              "each of the 7 digit groups has exactly one issuer");
 constexpr int kEpiCols = kTN / kEpiSlices;  // columns per epilogue thread
 constexpr int kCSm = kEpiCols / 2; // of those, prefetched into shared memory (the rest load in the final pass)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: default pipeline wait, and every teardown drain
