@@ -215,34 +215,9 @@ __global__ void slice_kernel(int row_blocks, int M, int N, int K, const double* 
 
 // ---------------------------------------------------------------- tensor-core update
 
-// T * 2^e rounded to nearest (even) in binary64, built with integer operations only
-// (the FP64 pipe of GB300 is narrow; this keeps the conversion off it).
-__device__ __forceinline__ double i64_times_pow2(long long T, int e) {
-  const unsigned long long sgn = (T < 0) ? 0x8000000000000000ull : 0ull;
-  unsigned long long a = (T < 0) ? (0ull - static_cast<unsigned long long>(T)) : static_cast<unsigned long long>(T);
-  int msb = 63 - __clzll(static_cast<long long>(a));
-  unsigned long long m;
-  if (msb <= 52) {
-    m = a << (52 - msb);
-  } else {
-    const int sh = msb - 52;
-    m = a >> sh;
-    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (m & 1ull))) ++m;
-    if (m == (1ull << 53)) {
-      m >>= 1;
-      ++msb;
-    }
-  }
-  const int biased = msb + e + 1023;
-  if (biased <= 0 || biased >= 2047) return ldexp(static_cast<double>(T), e);  // outside the normal range
-  return __longlong_as_double(static_cast<long long>(sgn | (static_cast<unsigned long long>(biased) << 52) |
-                                                     (m & 0xFFFFFFFFFFFFFull)));
-}
-
-
 // T * 2^e via the hardware conversion of T (correctly rounded) and an exponent add (exact
-// for normal results; the same value as i64_times_pow2, and faster in the epilogue).
+// for normal results).  One FP64-pipe conversion: an integer-only conversion (normalise,
+// round, assemble the bits) measured slower here, its integer work slowing the MMA issue.
 __device__ __forceinline__ double i64_to_double_pow2(long long T, int e) {
   const double d = __ll2double_rn(T);
   const long long bits = __double_as_longlong(d);
