@@ -959,8 +959,9 @@ def main():
     ap.add_argument("--update-sms", type=int, default=0,
                     help="SMs of the wide update under look-ahead (0 = library choice)")
     ap.add_argument("--x0-slices", type=int, default=None,
-                    help="digit slices of the mixed path's first inverse (default: 3 for mixed16384, 7 for "
-                         "mixedbatch4096, the fastest measured there)")
+                    help="digit slices of the mixed path's first inverse (default: 3 for mixed16384, the "
+                         "reduced-precision start (7 measured faster there at kappa 1e6: 0.73 s against 1.34 s); "
+                         "7 for mixedbatch4096, the fastest measured there)")
     ap.add_argument("--workers", type=int, default=16, help="mixedbatch4096: host workers (= streams)")
     ap.add_argument("--compare-fma", action="store_true", help="mixed workload: also time the FP64-FMA update GJ")
     ap.add_argument("--traffic", type=float, default=None,
